@@ -1,0 +1,365 @@
+"""Benchmark of local approximate GP prediction (Gramacy & Haaland,
+arXiv:1409.0074) on one or more GB300 GPUs.
+
+A step is one pass of the whole path -- bounding box and FP32 design copy,
+kNN candidates, greedy ALC local design, predictive equations -- over one
+batch of M predictive locations on the 8-d workload: N = 1e6 design points,
+n0 = 6, n = 50, N' = 1000, theta = 1, g = 1e-6, ray search with p = 8 rays,
+FP32 scoring and FP64 factor update.  Inputs are resident in HBM before the
+timed region; a 256 MB buffer is written before every step to flush L2.
+
+Prints one JSON line.  `value` is locations/sec over all ranks (weak scaling:
+every rank predicts its own M locations; there is no collective on the data
+path).  `--impl reference` times the FP64 CPU oracle instead, on a bounded
+sample per step.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # SMs x FP32 lanes x FMA x max clock
+FP64_PEAK_TFLOPS = 1.25                               # GB300 FP64 rate
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--M", type=int, default=100_000)
+    ap.add_argument("--N", type=int, default=1_000_000)
+    ap.add_argument("--search", default="ray", choices=["ray", "exhaustive"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the other search/precision forms")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--cpu-sample", type=int, default=0, help="oracle locations (0: 32 per core)")
+    return ap.parse_args()
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
+                    "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def kernel_flops(name, w, nevals_sum_j):
+    """Algorithmic FLOPs of one launch's worth of work (see the design notes):
+    kNN 3 N p per location; a ray evaluation at design size j costs
+    j^2 + j (triangular matvec) + 4 j (two dots) + (3p + 2) j (correlations);
+    the exhaustive FP32 scoring step j^2 + j + 4j per candidate."""
+    if name == "knn_stream":
+        return 3.0 * w["N"] * w["p"] * w["M_launch"]
+    if name == "design32_ray":
+        s1, s2 = nevals_sum_j      # sum over evaluations of j and of j^2
+        return s2 + (5 + 3 * w["p"] + 2) * s1
+    return None
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_1409_0074_gb300 import lagp
+    from paper_1409_0074_gb300 import workloads as W
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    w = W.large_8d(M=args.M, N=args.N, seed=rank)
+    N, p, M = w.N, w.p, w.M
+    s, pr = lagp.SEARCH[args.search], lagp.PRECISION[args.precision]
+    R = w.nrays
+    X, Y, Xr = (torch.from_numpy(a).to(dev) for a in (w.X, w.Y, w.Xref))
+    wsb = lagp.laGP_workspace_bytes(N, p, M, w.n, w.nc, R, s, pr)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    mean = torch.empty(M, dtype=torch.float64, device=dev)
+    s2 = torch.empty(M, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        flush.zero_()
+        lagp.laGP_build_and_predict(X, Y, Xr, w.n0, w.n, w.nc, w.theta, w.g, s, R, pr, mean, s2,
+                                    ws, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    rc, st = lagp.laGP_status(ws)
+    if rc != 0:
+        raise RuntimeError("device status %d after warm-up" % st)
+    torch.cuda.synchronize()
+    barrier(world)
+    lagp.laGP_profile(True)
+    with Clocks(torch.cuda.current_device()) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    lagp.laGP_profile(False)
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(ms, world)
+    prof = lagp.laGP_profile_read()
+    rc, st = lagp.laGP_status(ws)
+    if rc != 0:
+        raise RuntimeError("device status %d in the timed region" % st)
+    value = world * M * args.steps / (ms_max / 1e3)
+
+    # dominant kernel and its roofline
+    top = max(prof.items(), key=lambda kv: kv[1][0])
+    name, (tot_ms, launches) = top
+    trace = lagp.predict(X, Y, Xr, w.n0, w.n, w.nc, w.theta, w.g, search=args.search,
+                         nrays=R, precision=args.precision, want_trace=True)
+    nev = trace["nevals"].cpu().numpy()[:, : w.n - w.n0].astype(np.float64)
+    js = np.arange(w.n0, w.n, dtype=np.float64)
+    sum_j = float((nev * js[None, :]).sum())
+    sum_j2 = float((nev * js[None, :] ** 2).sum())
+    chunks = launches // args.steps
+    work = kernel_flops(name, dict(N=N, p=p, M_launch=M / max(chunks, 1)),
+                        (sum_j / max(chunks, 1), sum_j2 / max(chunks, 1)))
+    roof = None
+    if work is not None:
+        per_launch_ms = tot_ms / launches
+        achieved = work / (per_launch_ms / 1e3) / 1e12
+        roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz",
+                "launch_ms": per_launch_ms}
+    kernels = {k: {"ms_per_step": v[0] / args.steps, "launches": v[1],
+                   "share": v[0] / sum(x[0] for x in prof.values())} for k, v in prof.items()}
+    mean_evals = float(nev.sum(axis=1).mean() / (w.n - w.n0))
+    return dict(value=value, ms=ms_max, clocks=clk.summary(), roofline=roof, kernels=kernels,
+                gpu_launches=int(sum(v[1] for v in prof.values())), w=w, tensors=(X, Y, Xr),
+                evals_per_step=mean_evals, max_evals_per_step=float(nev.max()),
+                rmse=float(np.sqrt(np.mean((trace["mean"].cpu().numpy() - w.Ytrue) ** 2))))
+
+
+def run_e2e(args, w):
+    """Same metric through the host-buffer C entry point, copies included."""
+    import torch
+    from paper_1409_0074_gb300 import lagp
+    s, pr = lagp.SEARCH[args.search], lagp.PRECISION[args.precision]
+    R = w.nrays
+
+    def pinned(a):
+        t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        return t.numpy()
+
+    Xh, Yh, Rh = pinned(w.X), pinned(w.Y), pinned(w.Xref)
+    mean = torch.empty(w.M, dtype=torch.float64).pin_memory().numpy()
+    s2 = torch.empty(w.M, dtype=torch.float64).pin_memory().numpy()
+    wsb = lagp.laGP_host_workspace_bytes(w.N, w.p, w.M, w.n, w.nc, R, s, pr)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    call = lambda: lagp.laGP_build_and_predict_host(Xh, Yh, Rh, w.n0, w.n, w.nc, w.theta, w.g, s,
+                                                    R, pr, mean, s2, ws)
+    call()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        call()
+    dt = time.perf_counter() - t0
+    h2d = Xh.nbytes + Yh.nbytes + Rh.nbytes
+    return {"value": w.M * args.steps / dt, "unit": "locations/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": mean.nbytes + s2.nbytes}
+
+
+def run_extra(args, w, tensors, search, precision, M, steps=2):
+    """Locations/sec of another search/precision form on the first M locations."""
+    import torch
+    from paper_1409_0074_gb300 import lagp
+    X, Y, Xr = tensors
+    Xr = Xr[:M].contiguous()
+    s, pr = lagp.SEARCH[search], lagp.PRECISION[precision]
+    wsb = lagp.laGP_workspace_bytes(w.N, w.p, M, w.n, w.nc, w.nrays, s, pr)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    mean = torch.empty(M, dtype=torch.float64, device="cuda")
+    s2 = torch.empty(M, dtype=torch.float64, device="cuda")
+    go = lambda: lagp.laGP_build_and_predict(X, Y, Xr, w.n0, w.n, w.nc, w.theta, w.g, s,
+                                             w.nrays, pr, mean, s2, ws)
+    go()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        go()
+    e1.record()
+    torch.cuda.synchronize()
+    rmse = float(np.sqrt(np.mean((mean.cpu().numpy() - w.Ytrue[:M]) ** 2)))
+    return {"locations_per_s": M * steps / (e0.elapsed_time(e1) / 1e3), "locations": M,
+            "rmse": rmse}
+
+
+def run_cpu_baseline(args, w, search, sample=None):
+    """The FP64 oracle as it stands, OpenMP over locations on the host cores."""
+    import oracle
+    cores = os.cpu_count() or 1
+    S = sample or args.cpu_sample or 32 * cores
+    S = min(S, w.M)
+    t0 = time.perf_counter()
+    r = oracle.predict(w.X, w.Y, w.Xref[:S], w.n0, w.n, w.nc, w.theta, w.g, search,
+                       nrays=w.nrays, nthreads=0)
+    dt = time.perf_counter() - t0
+    return {"value": S / dt, "unit": "locations/s", "cores": int(r["threads"]), "kind": "oracle",
+            "sample": "first %d of the %d locations, %s search, FP64" % (S, w.M, search),
+            "seconds": dt}
+
+
+def base_line(args, world, value, ms, w):
+    return {"metric": "locations/sec at N=1e6,d=8,n=50 (ray search)", "value": value,
+            "unit": "locations/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps if ms is not None else None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "data": "synthetic (seeded uniform design, sinusoid-plus-product response)",
+            "config": {"workload": w.name, "N": w.N, "p": w.p, "M": w.M, "n0": w.n0, "n": w.n,
+                       "N_close": w.nc, "theta": w.theta, "g": w.g, "search": args.search,
+                       "nrays": w.nrays,
+                       "precision": "fp32 scoring, fp64 update" if args.precision == "fp32"
+                       else "fp64", "l2": "flushed: 256 MB written before every step",
+                       "parallelism": "locations sharded over %d rank(s)" % world}}
+
+
+def main():
+    args = parse()
+    rank, world = dist_init(args)
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        from paper_1409_0074_gb300 import workloads as W
+        w = W.large_8d(M=args.M, N=args.N)
+        cores = os.cpu_count() or 1
+        S = args.cpu_sample or 8 * cores
+        if args.warmup > 0:   # one short untimed pass (page-in, thread start-up)
+            run_cpu_baseline(args, w, args.search, sample=min(S, cores))
+        t0 = time.perf_counter()
+        rates = [run_cpu_baseline(args, w, args.search, sample=S) for _ in range(args.steps)]
+        dt = time.perf_counter() - t0
+        value = S * args.steps / dt
+        line = base_line(args, 1, value, dt * 1e3, w)
+        line.update({"impl": "reference", "dtype": "f64",
+                     "cpu_baseline": {"value": value, "unit": "locations/s",
+                                      "cores": rates[0]["cores"], "kind": "oracle",
+                                      "sample": "%d locations per step" % S},
+                     "e2e": {"value": value, "unit": "locations/s", "h2d_bytes_per_step": 0,
+                             "d2h_bytes_per_step": 0}})
+        print(json.dumps(line))
+        return
+
+    r = run_ours(args, rank, world)
+    w = r["w"]
+    line = base_line(args, world, r["value"], r["ms"], w)
+    line.update({"dtype": "f32/f64" if args.precision == "fp32" else "f64",
+                 "roofline": r["roofline"], "clocks": r["clocks"],
+                 "gpu_launches": r["gpu_launches"], "kernels": r["kernels"],
+                 "rmse": r["rmse"], "ray_evals_per_step": r["evals_per_step"],
+                 "ray_evals_per_step_max": r["max_evals_per_step"]})
+    if world == 1:
+        line["e2e"] = run_e2e(args, w)
+        if not args.no_extras:
+            ex = {}
+            ex["exhaustive_fp32"] = run_extra(args, w, r["tensors"], "exhaustive", "fp32",
+                                              min(w.M, 20000))
+            ex["ray_fp64"] = run_extra(args, w, r["tensors"], "ray", "fp64", min(w.M, 4000))
+            ex["exhaustive_fp64"] = run_extra(args, w, r["tensors"], "exhaustive", "fp64",
+                                              min(w.M, 1000), steps=1)
+            line["other_forms"] = ex
+        if not args.no_cpu:
+            line["cpu_baseline"] = run_cpu_baseline(args, w, args.search)
+    else:
+        line["e2e"] = None
+    if rank == 0:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * lagp.h -- C ABI of the GB300 (sm_103a) library for local approximate
+ * Gaussian process prediction with greedy ALC local designs.
+ *
+ * Method: Gramacy & Haaland, "Speeding up neighborhood search in local
+ * Gaussian process prediction" (arXiv:1409.0074).  For every predictive
+ * location x:
+ *   1. the N_close nearest design points are the candidates (Sec 2.2);
+ *   2. the local design starts from the n0 nearest candidates;
+ *   3. for j = n0 .. n-1 one candidate is added, the one maximising the
+ *      reduction in predictive variance at x (ALC, the integrand of Eq. alc),
+ *      found by exhaustive scoring of every unselected candidate (Sec 2.2) or
+ *      by the ray search of Sec 4 (Brent line searches along rays leaving x,
+ *      the best point snapped to the nearest unselected candidate); K_j^{-1}
+ *      is extended by the partitioned-inverse update (Sec 2.2);
+ *   4. the predictive mean and scale of Eq. predgp and Eq. preds2 are returned
+ *      (Student-t with n degrees of freedom).
+ * Correlation: isotropic Gaussian exp(-||x - x'||^2 / theta) with nugget g on
+ * self-correlations (Sec 2.1).
+ *
+ * Conventions for every entry point below:
+ *   - Pointers marked "device" are CUDA device pointers; "host" are host
+ *     pointers.  Arrays are dense, row-major, binary64 unless stated.
+ *   - The caller owns every buffer.  The library allocates no device memory:
+ *     scratch space comes from the caller's `workspace`, sized by
+ *     laGP_workspace_bytes.  The library never frees caller memory.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Device entry
+ *     points only enqueue work; a return of LAGP_OK means "enqueued".  Errors
+ *     found on the device are collected in a status word inside the workspace,
+ *     read by laGP_status.
+ *   - Errors are returned as negative codes; nothing is printed.
+ */
+#ifndef LAGP_H
+#define LAGP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Search for the next design point (Sec 2.2 exhaustive, Sec 4 rays). */
+#define LAGP_EXHAUSTIVE 0
+#define LAGP_RAY 1
+
+/* Arithmetic of the greedy loop.
+ * LAGP_FP64: every step in binary64 with the paper's explicit K_j^{-1} and
+ *   partitioned-inverse update, in a fixed operation order (the parity form).
+ * LAGP_FP32_SCORE: candidate and ray scoring in FP32 through the inverse
+ *   Cholesky factor L_j^{-1} (k^T K^{-1} k = |L^{-1} k|^2); the factor update,
+ *   its Schur complement and the predictive equations stay in binary64. */
+#define LAGP_FP64 0
+#define LAGP_FP32_SCORE 1
+
+/* Return codes. */
+#define LAGP_OK 0
+#define LAGP_ERR_INVALID (-1)   /* an argument is out of range or a pointer is NULL */
+#define LAGP_ERR_WORKSPACE (-2) /* workspace_bytes is below laGP_workspace_bytes */
+#define LAGP_ERR_CUDA (-3)      /* a CUDA call or kernel launch failed */
+#define LAGP_ERR_DEVICE (-4)    /* laGP_status: the device reported a failure */
+
+/* Device status bits reported by laGP_status. */
+#define LAGP_STATUS_TIMEOUT 1u      /* a bounded on-device wait ran out */
+#define LAGP_STATUS_CAPACITY 2u     /* too many exactly tied kNN distances */
+#define LAGP_STATUS_NUMERIC 4u      /* a Schur complement v <= 0: that location's
+                                       mean and s2 are NaN */
+
+/*
+ * Bytes of device workspace laGP_build_and_predict needs for these sizes.
+ * Arguments as in laGP_build_and_predict (n and N_close are the maxima when
+ * per-location arrays are used).  Returns 0 when the sizes are invalid.
+ */
+size_t laGP_workspace_bytes(int64_t N, int p, int64_t M, int n, int N_close, int nrays,
+                            int search, int precision);
+
+/*
+ * Local approximate GP prediction at M locations (steps 1-4 above).
+ *
+ *   design    device [N][p]   design X_N
+ *   y         device [N]      responses Y_N
+ *   N, p      design size (N >= N_close) and input dimension (1 <= p <= 16)
+ *   xref      device [M][p]   predictive locations
+ *   M         number of locations (>= 0; 0 is a no-op)
+ *   n0        starting design size (1 <= n0 <= n)
+ *   n         final local design size (n <= N_close, n <= 128)
+ *   N_close   candidates per location (n <= N_close <= min(N, 4096))
+ *   theta     lengthscale (> 0)
+ *   g         nugget (>= 0)
+ *   search    LAGP_EXHAUSTIVE or LAGP_RAY
+ *   nrays     rays per step for LAGP_RAY (<= 0 selects p; at most 16 and at
+ *             most N_close - n); ignored for LAGP_EXHAUSTIVE
+ *   precision LAGP_FP64 or LAGP_FP32_SCORE
+ *   n_loc     device [M] int32 or NULL: per-location final size (each in
+ *             [n0, n]); NULL gives every location n
+ *   nclose_loc device [M] int32 or NULL: per-location N_close (each in
+ *             [that location's n, N_close]); NULL gives N_close
+ *   mean      device [M] out: predictive mean, Eq. predgp
+ *   s2        device [M] out: predictive scale sigma^2, Eq. preds2, with
+ *             K(x,x) = 1 + g; the degrees of freedom are the location's n and
+ *             the predictive variance is s2 * n / (n - 2)
+ *   selected  device [M][n] int32 out or NULL: design indices in selection
+ *             order (the n0 nearest first); entries past a location's n are -1
+ *   tie_gap   device [M][n] out or NULL: entry j - n0 holds the smallest
+ *             relative gap among the comparisons that decided step j (argmax
+ *             of ALC; for rays also Brent's comparisons, the s = 0 check and
+ *             the snap); 0 elsewhere
+ *   nevals    device [M][n] int32 out or NULL: ALC evaluations of ray step j
+ *             at entry j - n0 (0 for the exhaustive search)
+ *   workspace device scratch of workspace_bytes >= laGP_workspace_bytes(...)
+ *   stream    cudaStream_t
+ *
+ * A location whose update meets v <= 0 gets NaN in mean and s2 and sets
+ * LAGP_STATUS_NUMERIC; the other locations are unaffected.
+ */
+int laGP_build_and_predict(const double* design, const double* y, int64_t N, int p,
+                           const double* xref, int64_t M, int n0, int n, int N_close,
+                           double theta, double g, int search, int nrays, int precision,
+                           const int32_t* n_loc, const int32_t* nclose_loc, double* mean,
+                           double* s2, int32_t* selected, double* tie_gap, int32_t* nevals,
+                           void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Step 1 alone (Sec 2.2): the N_close nearest design points of each location,
+ * ordered by squared Euclidean distance computed in binary64 as
+ * sum_k (X_ik - x_k)^2 (ascending k), ties to the lower index.
+ *   cand      device [M][N_close] int32 out
+ *   workspace sized by laGP_knn_workspace_bytes(N, p, M, N_close)
+ */
+size_t laGP_knn_workspace_bytes(int64_t N, int p, int64_t M, int N_close);
+int laGP_knn(const double* design, int64_t N, int p, const double* xref, int64_t M,
+             int N_close, int32_t* cand, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Waits for `stream`, then reads and clears the device status word of the
+ * workspace.  *status receives the LAGP_STATUS_* bits.  Returns LAGP_OK when
+ * no bit was set, LAGP_ERR_DEVICE when one was, LAGP_ERR_CUDA when the wait
+ * or the copy failed.
+ */
+int laGP_status(void* workspace, void* stream, unsigned* status);
+
+/*
+ * Host-buffer form of laGP_build_and_predict: design, y, xref, n_loc,
+ * nclose_loc, mean, s2, selected, tie_gap and nevals are HOST pointers (pinned
+ * memory makes the copies asynchronous with respect to the host).  Inputs are
+ * copied into the device workspace, the device path runs on `stream`, the
+ * outputs are copied back and the stream is synchronised before returning;
+ * device-side status bits are returned as LAGP_ERR_DEVICE.
+ *   workspace device scratch of at least laGP_host_workspace_bytes(...)
+ */
+size_t laGP_host_workspace_bytes(int64_t N, int p, int64_t M, int n, int N_close, int nrays,
+                                 int search, int precision);
+int laGP_build_and_predict_host(const double* design, const double* y, int64_t N, int p,
+                                const double* xref, int64_t M, int n0, int n, int N_close,
+                                double theta, double g, int search, int nrays, int precision,
+                                const int32_t* n_loc, const int32_t* nclose_loc, double* mean,
+                                double* s2, int32_t* selected, double* tie_gap, int32_t* nevals,
+                                void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Opt-in kernel timing.  laGP_profile(1) clears earlier records and makes
+ * every later call record a pair of CUDA events on its stream around each
+ * kernel it launches; laGP_profile(0) stops recording.  Not thread-safe
+ * against concurrent callers of the other entry points.
+ * laGP_profile_read waits for the recorded events and aggregates them by
+ * kernel name: names [max_kernels][32] (NUL-terminated), total_ms and
+ * launches [max_kernels].  Returns the number of kernels filled in, or a
+ * negative error code.
+ */
+int laGP_profile(int enable);
+int laGP_profile_read(int max_kernels, char* names, double* total_ms, int32_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LAGP_H */

@@ -1,0 +1,125 @@
+// common.cuh -- device helpers shared by the CUDA kernels of the laGP library.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define LAGP_MAX_P 16        // input dimension limit
+#define LAGP_MAX_N 128       // local design size limit
+#define LAGP_MAX_RAYS 16     // rays per greedy step limit
+#define LAGP_KNN_TILE 256    // design points per streamed kNN tile
+
+// Device status bits (written with atomicOr into the workspace status word).
+#define LAGP_DEV_TIMEOUT 1u        // a bounded wait ran out
+#define LAGP_DEV_KNN_OVERFLOW 2u   // more tied kNN candidates than the buffer holds
+#define LAGP_DEV_BAD_UPDATE 4u     // a Schur complement v <= 0 (location gets NaN)
+
+// Bound of every mbarrier wait, in SM clock cycles (about 2 s at 2 GHz).
+#define LAGP_WAIT_CYCLES 4000000000ll
+
+namespace lagp {
+
+// exp(x) in binary64 by Cody & Waite (1980) argument reduction x = k ln2 + r,
+// |r| <= ln2/2, the degree-13 Taylor polynomial of e^r by Horner's rule, and an
+// exact scaling by 2^k.  Results below the normal range (x < -708) are 0.
+// Every operation is an explicitly rounded multiply or add, so the value does
+// not depend on compiler contraction.  The FP64 parity path uses it so that
+// correlations are reproducible bit for bit on any IEEE-754 machine.
+__device__ __forceinline__ double exp_cw(double x) {
+  if (x != x) return x;
+  if (x > 709.0) return __longlong_as_double(0x7ff0000000000000ll);
+  if (x < -708.0) return 0.0;
+  const double inv_ln2 = 0x1.71547652b82fep+0;
+  const double ln2_hi = 0x1.62e42fee00000p-1;
+  const double ln2_lo = 0x1.a39ef35793c76p-33;
+  double kd = rint(__dmul_rn(x, inv_ln2));
+  double r = __dsub_rn(__dsub_rn(x, __dmul_rn(kd, ln2_hi)), __dmul_rn(kd, ln2_lo));
+  double s = 1.0 / 6227020800.0;
+  s = __dadd_rn(__dmul_rn(s, r), 1.0 / 479001600.0);
+  s = __dadd_rn(__dmul_rn(s, r), 1.0 / 39916800.0);
+  s = __dadd_rn(__dmul_rn(s, r), 1.0 / 3628800.0);
+  s = __dadd_rn(__dmul_rn(s, r), 1.0 / 362880.0);
+  s = __dadd_rn(__dmul_rn(s, r), 1.0 / 40320.0);
+  s = __dadd_rn(__dmul_rn(s, r), 1.0 / 5040.0);
+  s = __dadd_rn(__dmul_rn(s, r), 1.0 / 720.0);
+  s = __dadd_rn(__dmul_rn(s, r), 1.0 / 120.0);
+  s = __dadd_rn(__dmul_rn(s, r), 1.0 / 24.0);
+  s = __dadd_rn(__dmul_rn(s, r), 1.0 / 6.0);
+  s = __dadd_rn(__dmul_rn(s, r), 0.5);
+  s = __dadd_rn(__dmul_rn(s, r), 1.0);
+  s = __dadd_rn(__dmul_rn(s, r), 1.0);
+  return ldexp(s, (int)kd);
+}
+
+// Squared distance in binary64, ascending coordinate order, no contraction.
+__device__ __forceinline__ double sqdist64(const double* a, const double* b, int p) {
+  double acc = 0.0;
+  for (int k = 0; k < p; ++k) {
+    double t = __dsub_rn(a[k], b[k]);
+    acc = __dadd_rn(acc, __dmul_rn(t, t));
+  }
+  return acc;
+}
+
+// Isotropic Gaussian correlation exp(-||a-b||^2 / theta) in binary64.
+__device__ __forceinline__ double corr64(const double* a, const double* b, int p, double theta) {
+  return exp_cw(-(__ddiv_rn(sqdist64(a, b, p), theta)));
+}
+
+__device__ __forceinline__ double relgap64(double a, double b) {
+  double m = fmax(fabs(a), fabs(b));
+  if (m == 0.0) return 0.0;
+  return __ddiv_rn(fabs(__dsub_rn(a, b)), m);
+}
+
+__device__ __forceinline__ int ray_offset(int j, int n0) {
+  int t = j - n0 + 1;
+  if (t < 1) return 0;
+  int q = 1;
+  while ((q + 1) * (q + 1) <= t) ++q;
+  return t % q;
+}
+
+// ----- mbarrier / bulk-copy (TMA) helpers -----------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// 1-D bulk copy global -> shared, completion signalled on the mbarrier.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// Waits for phase `parity` of the barrier; gives up after LAGP_WAIT_CYCLES
+// and returns false (the caller records LAGP_DEV_TIMEOUT and stops).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t addr = smem_u32(bar);
+  const long long t0 = clock64();
+  while (clock64() - t0 < LAGP_WAIT_CYCLES) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+}  // namespace lagp

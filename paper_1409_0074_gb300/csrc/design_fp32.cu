@@ -1,0 +1,598 @@
+// design_fp32.cu -- greedy local design with FP32 candidate scoring and an
+// FP64 factor update, one CTA per predictive location.
+//
+// Scoring form.  With K_j = L_j L_j^T (Cholesky) the ALC integrand of Eq. alc
+// (sign reading as in the FP64 path) becomes
+//     w = L_j^{-1} k_j(x'),  v = (1 + g) - |w|^2,
+//     ALC(x') = (w . z - K(x', x))^2 / v,   z = L_j^{-1} k_j(x),
+// the same quadratic forms as k^T K^{-1} k, evaluated through the inverse
+// factor.  In FP32 this keeps the error of v near eps * sqrt(cond K) instead of
+// eps * cond K: on the 8-d, N = 1e6 workload (cond K_50 ~ 1e6, v ~ 1e-4) an
+// explicit-inverse FP32 score has errors as large as v itself, while the
+// factored score stays near 5e-6.
+//
+// FP64 state (the partitioned update, Sec 2.2, in factored form): appending
+// x_new with l = L_j^{-1} k_j(x_new), v = (1 + g) - |l|^2 (the Schur complement
+// of the paper's update), d = sqrt(v) gives
+//     L_{j+1}^{-1} = [[L_j^{-1}, 0], [-(L_j^{-T} l)^T / d, 1 / d]],
+// so one new row per step, O(j^2).  z and L^{-1} y grow by one entry per step
+// and the predictive equations (Eq. predgp, preds2) follow as
+//     mu = z . (L^{-1} y),  psi = |L^{-1} y|^2,  sigma^2 = psi (1 + g - |z|^2) / n.
+// Scoring coordinates are FP32 and centred on the design's bounding box.
+#include <cstdint>
+
+#include "common.cuh"
+#include "lagp_internal.h"
+
+namespace lagp {
+
+#define D32_THREADS 256
+#define D32_WARPS (D32_THREADS / 32)
+// candidates scored per pass of the exhaustive search (shared-memory tile rows)
+__host__ __device__ __forceinline__ int exh_pass(int n_max) { return n_max <= 64 ? 256 : 128; }
+
+struct D32Params {
+  const double* X;
+  const double* Y;
+  int p, PP;
+  const float* Xf;       // centred FP32 design [Npad][PP]
+  const double* xref;
+  int64_t M;
+  const int32_t* cand;
+  int nc_max;
+  const int32_t* nc_loc;
+  int n0, n_max;
+  const int32_t* n_loc;
+  double theta, g;
+  int R;
+  const double* lo;
+  const double* hi;
+  const double* center;
+  double* mean;
+  double* s2;
+  int32_t* selected;
+  double* tie_gap;
+  int32_t* nevals;
+  double* Linv;          // [M][n_max][n_max] FP64 inverse factor
+  float* Kc;             // exhaustive: [M][n_max][nc_max] FP32 correlation cache
+  unsigned* status;
+};
+
+struct L32 {
+  float* Lf;       // [n_max][ldf] FP32 copy of L^{-1}
+  float* zf;       // [n_max]
+  float* Sf;       // [n_max][PP] centred FP32 selected coordinates
+  float* xf;       // [PP]
+  float* lof;      // [PP]
+  float* hif;      // [PP]
+  float* kzf;      // [WARPS][n_max]  (exhaustive: [exh_pass][ldf] tile)
+  float* rz;       // [WARPS][PP]
+  float* rA;       // [R][PP]
+  float* rE;       // [R][PP]
+  float* ralc;     // [R]
+  float* rs;       // [R]
+  float* xs;       // [PP]
+  float* red;      // [WARPS*4]
+  double* S64;     // [n_max][p]
+  double* xq;      // [p]
+  double* kvec;    // [n_max]
+  double* l;       // [n_max]
+  double* z;       // [n_max]
+  double* zy;      // [n_max]
+  double* kx;      // [n_max]
+  double* dred;    // [WARPS*4]
+  double* dscal;   // [4]
+  int* sel;        // [n_max]
+  int* starts;     // [R]
+  int* rnev;       // [R]
+  int* ired;       // [WARPS*2]
+  unsigned char* used;
+  int j, ldf;
+  float neg_inv_theta, onepg;
+};
+
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sumd(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+// block sum of up to 2 doubles; all threads receive the result
+__device__ void block_sum2(double& a, double& b, double* scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  a = warp_sumd(a);
+  b = warp_sumd(b);
+  if (lane == 0) { scratch[2 * warp] = a; scratch[2 * warp + 1] = b; }
+  __syncthreads();
+  a = 0.0; b = 0.0;
+  for (int w = 0; w < D32_WARPS; ++w) { a += scratch[2 * w]; b += scratch[2 * w + 1]; }
+  __syncthreads();
+}
+
+// best (value, index) over the block: larger value wins, ties to the lower index
+struct VI { float v; int i; float v2; };
+__device__ __forceinline__ VI vi_merge_max(VI a, VI b) {
+  VI r;
+  if (b.v > a.v || (b.v == a.v && b.i >= 0 && (a.i < 0 || b.i < a.i))) {
+    r.v = b.v; r.i = b.i; r.v2 = fmaxf(a.v, b.v2);
+  } else {
+    r.v = a.v; r.i = a.i; r.v2 = fmaxf(a.v2, b.v);
+  }
+  return r;
+}
+__device__ VI block_best(VI t, float* fs, int* is) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) {
+    VI u;
+    u.v = __shfl_xor_sync(0xffffffffu, t.v, o);
+    u.i = __shfl_xor_sync(0xffffffffu, t.i, o);
+    u.v2 = __shfl_xor_sync(0xffffffffu, t.v2, o);
+    t = vi_merge_max(t, u);
+  }
+  if (lane == 0) { fs[2 * warp] = t.v; fs[2 * warp + 1] = t.v2; is[warp] = t.i; }
+  __syncthreads();
+  VI r; r.v = fs[0]; r.v2 = fs[1]; r.i = is[0];
+  for (int w = 1; w < D32_WARPS; ++w) {
+    VI u; u.v = fs[2 * w]; u.v2 = fs[2 * w + 1]; u.i = is[w];
+    r = vi_merge_max(r, u);
+  }
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ const float* cand_f(const D32Params& P, const int32_t* cl, int r) {
+  return P.Xf + (int64_t)cl[r] * P.PP;
+}
+
+// Append candidate rank r: FP64 factor row, z, L^{-1}y, FP32 copies.
+template <int SEARCH>
+__device__ bool add_point32(const D32Params& P, L32& L, const int32_t* cl, int nc, int r,
+                            double* Lg, float* Kc_loc) {
+  const int tid = threadIdx.x, p = P.p, j = L.j, ld = P.n_max;
+  const double* c = P.X + (int64_t)cl[r] * p;
+  if (tid < p) L.S64[j * p + tid] = c[tid];
+  if (tid < P.PP) L.Sf[j * P.PP + tid] = cand_f(P, cl, r)[tid];
+  __syncthreads();
+  for (int i = tid; i < j; i += blockDim.x) L.kvec[i] = corr64(L.S64 + i * p, L.S64 + j * p, p, P.theta);
+  __syncthreads();
+  double vv = 0.0, dummy = 0.0;
+  for (int i = tid; i < j; i += blockDim.x) {
+    const double* Li = Lg + (int64_t)i * ld;
+    double acc = 0.0;
+    for (int k = 0; k <= i; ++k) acc = fma(Li[k], L.kvec[k], acc);
+    L.l[i] = acc;
+    vv = fma(acc, acc, vv);
+  }
+  block_sum2(vv, dummy, L.dred);
+  const double v = (1.0 + P.g) - vv;
+  if (!(v > 0.0)) return false;
+  const double inv_d = 1.0 / sqrt(v);
+  for (int k = tid; k < j; k += blockDim.x) {
+    double acc = 0.0;
+    for (int i = k; i < j; ++i) acc = fma(L.l[i], Lg[(int64_t)i * ld + k], acc);
+    const double rk = -acc * inv_d;
+    Lg[(int64_t)j * ld + k] = rk;
+    L.Lf[j * L.ldf + k] = (float)rk;
+  }
+  if (tid == 0) {
+    Lg[(int64_t)j * ld + j] = inv_d;
+    L.Lf[j * L.ldf + j] = (float)inv_d;
+    L.kx[j] = corr64(L.S64 + j * p, L.xq, p, P.theta);
+    L.sel[j] = r;
+    L.used[r] = 1;
+  }
+  __syncthreads();
+  // z_j = row_j . k(x), (L^{-1} y)_j = row_j . y_S
+  double zz = 0.0, zyy = 0.0;
+  for (int k = tid; k <= j; k += blockDim.x) {
+    const double rk = Lg[(int64_t)j * ld + k];
+    zz = fma(rk, L.kx[k], zz);
+    zyy = fma(rk, P.Y[cl[L.sel[k]]], zyy);
+  }
+  block_sum2(zz, zyy, L.dred);
+  if (tid == 0) {
+    L.z[j] = zz;
+    L.zy[j] = zyy;
+    L.zf[j] = (float)zz;
+  }
+  if (SEARCH == 0) {
+    float* row = Kc_loc + (int64_t)j * P.nc_max;
+    const float* sj = L.Sf + j * P.PP;
+    for (int q = tid; q < nc; q += blockDim.x) {
+      const float* cq = cand_f(P, cl, q);
+      float d = 0.f;
+      for (int k = 0; k < P.PP; ++k) { float t = cq[k] - sj[k]; d = fmaf(t, t, d); }
+      row[q] = __expf(d * L.neg_inv_theta);
+    }
+  }
+  __syncthreads();
+  L.j = j + 1;
+  return true;
+}
+
+// ----- exhaustive search, CUDA-core FP32 scoring ---------------------------------
+__device__ int search_exh32(const D32Params& P, L32& L, const int32_t* cl, int nc,
+                            const float* Kc_loc, double* gap_out) {
+  const int tid = threadIdx.x, j = L.j, ldt = L.ldf;
+  float* T = L.kzf;   // [pass][ldt]
+  const int pass = exh_pass(P.n_max);
+  VI best; best.v = -1.f; best.v2 = -1.f; best.i = -1;
+  for (int base = 0; base < nc; base += pass) {
+    const int cnt = min(pass, nc - base);
+    // stage the pass's correlation rows, transposed: T[r][i] = K(S_i, c_r)
+    for (int e = tid; e < j * pass; e += blockDim.x) {
+      const int i = e / pass, rr = e - i * pass;
+      if (rr < cnt) T[rr * ldt + i] = Kc_loc[(int64_t)i * P.nc_max + base + rr];
+    }
+    __syncthreads();
+    const int r = base + tid;
+    if (tid < cnt && !L.used[r]) {
+      const float* kc = T + tid * ldt;
+      float vs = 0.f, ns = 0.f;
+      for (int i = 0; i < j; ++i) {
+        const float* Li = L.Lf + i * ldt;
+        float a0 = 0.f, a1 = 0.f;
+        int k = 0;
+        for (; k + 1 <= i; k += 2) { a0 = fmaf(Li[k], kc[k], a0); a1 = fmaf(Li[k + 1], kc[k + 1], a1); }
+        if (k <= i) a0 = fmaf(Li[k], kc[k], a0);
+        const float w = a0 + a1;
+        vs = fmaf(w, w, vs);
+        ns = fmaf(w, L.zf[i], ns);
+      }
+      const float* cr = cand_f(P, cl, r);
+      float d = 0.f;
+      for (int k = 0; k < P.PP; ++k) { float t = cr[k] - L.xf[k]; d = fmaf(t, t, d); }
+      const float v = L.onepg - vs;
+      const float num = ns - __expf(d * L.neg_inv_theta);
+      const float alc = v > 0.f ? num * num / v : 0.f;
+      if (alc > best.v) { best.v2 = best.v; best.v = alc; best.i = r; }
+      else if (alc > best.v2) best.v2 = alc;
+    }
+    __syncthreads();
+  }
+  VI b = block_best(best, L.red, L.ired);
+  *gap_out = (b.v > 0.f && b.v2 >= 0.f) ? (double)((b.v - b.v2) / b.v) : 0.0;
+  return b.i;
+}
+
+// ----- ray search, FP32 evaluations (Sec 4) ---------------------------------------
+__device__ float warp_alc32(const D32Params& P, L32& L, const float* z) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = L.j, PP = P.PP, ldt = L.ldf;
+  float* kz = L.kzf + warp * P.n_max;
+  for (int i = lane; i < j; i += 32) {
+    const float* s = L.Sf + i * PP;
+    float d = 0.f;
+    for (int k = 0; k < PP; ++k) { float t = s[k] - z[k]; d = fmaf(t, t, d); }
+    kz[i] = __expf(d * L.neg_inv_theta);
+  }
+  __syncwarp();
+  float vs = 0.f, ns = 0.f;
+  for (int i = lane; i < j; i += 32) {
+    const float* Li = L.Lf + i * ldt;
+    float a0 = 0.f, a1 = 0.f;
+    int k = 0;
+    for (; k + 1 <= i; k += 2) { a0 = fmaf(Li[k], kz[k], a0); a1 = fmaf(Li[k + 1], kz[k + 1], a1); }
+    if (k <= i) a0 = fmaf(Li[k], kz[k], a0);
+    const float w = a0 + a1;
+    vs = fmaf(w, w, vs);
+    ns = fmaf(w, L.zf[i], ns);
+  }
+  vs = warp_sum(vs);
+  ns = warp_sum(ns);
+  float d = 0.f;
+  for (int k = 0; k < PP; ++k) { float t = z[k] - L.xf[k]; d = fmaf(t, t, d); }
+  __syncwarp();
+  const float v = L.onepg - vs;
+  const float num = ns - __expf(d * L.neg_inv_theta);
+  return v > 0.f ? num * num / v : 0.f;
+}
+
+__device__ float ray_f32(const D32Params& P, L32& L, const float* A, const float* E, float s) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* z = L.rz + warp * P.PP;
+  if (lane < P.PP) z[lane] = fmaf(s, E[lane] - A[lane], A[lane]);
+  __syncwarp();
+  return -warp_alc32(P, L, z);
+}
+
+// Brent (1973) fmin on [0,1] in FP32 arithmetic, same constants as the FP64 path.
+__device__ float brent32(const D32Params& P, L32& L, const float* A, const float* E, float* xmin,
+                         int* nev) {
+  const float tol = 0x1p-13f, sqrt_eps = 0x1p-26f;
+  const float golden = 0.381966011250105151795f;
+  const float tol3 = tol / 3.f;
+  float a = 0.f, b = 1.f;
+  float x = a + golden * (b - a);
+  float w = x, v = x;
+  float fx = ray_f32(P, L, A, E, x);
+  float fw = fx, fv = fx, d = 0.f, e = 0.f;
+  int evals = 1;
+  for (int it = 0; it < 1000; ++it) {
+    const float m = 0.5f * (a + b);
+    const float tol1 = sqrt_eps * fabsf(x) + tol3;
+    const float tol2 = 2.f * tol1;
+    if (fabsf(x - m) <= tol2 - 0.5f * (b - a)) break;
+    bool golden_step = true;
+    if (fabsf(e) > tol1) {
+      float r = (x - w) * (fx - fv);
+      float q = (x - v) * (fx - fw);
+      float pn = (x - v) * q - (x - w) * r;
+      q = 2.f * (q - r);
+      if (q > 0.f) pn = -pn; else q = -q;
+      const float e_prev = e;
+      e = d;
+      if (fabsf(pn) < fabsf(0.5f * q * e_prev) && pn > q * (a - x) && pn < q * (b - x)) {
+        d = pn / q;
+        const float u_try = x + d;
+        if (u_try - a < tol2 || b - u_try < tol2) d = (m - x >= 0.f) ? tol1 : -tol1;
+        golden_step = false;
+      }
+    }
+    if (golden_step) {
+      e = (x < m) ? (b - x) : (a - x);
+      d = golden * e;
+    }
+    float u;
+    if (fabsf(d) >= tol1) u = x + d;
+    else if (d >= 0.f) u = x + tol1;
+    else u = x - tol1;
+    const float fu = ray_f32(P, L, A, E, u);
+    ++evals;
+    if (fu <= fx) {
+      if (u < x) b = x; else a = x;
+      v = w; fv = fw;
+      w = x; fw = fx;
+      x = u; fx = fu;
+    } else {
+      if (u < x) a = u; else b = u;
+      if (fu <= fw || w == x) {
+        v = w; fv = fw;
+        w = u; fw = fu;
+      } else if (fu <= fv || v == x || v == w) {
+        v = u; fv = fu;
+      }
+    }
+  }
+  *xmin = x;
+  *nev = evals;
+  return fx;
+}
+
+__device__ int search_ray32(const D32Params& P, L32& L, const int32_t* cl, int nc, double* gap_out,
+                            int* nev_out) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int PP = P.PP, R = P.R, j = L.j;
+  if (tid == 0) {
+    // starts: unselected candidates of rank k0, k0+1, ..., k0+R-1 (mod |U|)
+    const int nU = nc - j;
+    const int k0 = ray_offset(j, P.n0);
+    int seen = 0;
+    for (int r = 0; r < nc && seen < k0 + R; ++r) {
+      if (L.used[r]) continue;
+      const int t = seen - k0;
+      if (t >= 0) L.starts[t] = r;
+      ++seen;
+    }
+    for (int t = 0; t < R; ++t) {
+      if (k0 + t < nU) continue;
+      const int target = (k0 + t) % nU;
+      int s2 = 0, r = 0;
+      for (; r < nc; ++r) { if (L.used[r]) continue; if (s2 == target) break; ++s2; }
+      L.starts[t] = r < nc ? r : nc - 1;
+    }
+  }
+  __syncthreads();
+  for (int i = warp; i < R; i += D32_WARPS) {
+    float* A = L.rA + i * PP;
+    float* E = L.rE + i * PP;
+    if (lane < PP) A[lane] = cand_f(P, cl, L.starts[i])[lane];
+    __syncwarp();
+    if (lane == 0) {
+      float tau = 1.f;
+      for (int k = 0; k < P.p; ++k) {
+        const float dk = 10.f * (A[k] - L.xf[k]);
+        if (dk > 0.f) tau = fminf(tau, (L.hif[k] - A[k]) / dk);
+        else if (dk < 0.f) tau = fminf(tau, (L.lof[k] - A[k]) / dk);
+      }
+      tau = fmaxf(tau, 0.f);
+      for (int k = 0; k < PP; ++k) E[k] = fmaf(tau, 10.f * (A[k] - L.xf[k]), A[k]);
+    }
+    __syncwarp();
+    const float alc0 = warp_alc32(P, L, A);
+    int evals = 1;
+    float s_star = 0.f, alc_star = alc0;
+    float len2 = 0.f;
+    for (int k = 0; k < PP; ++k) { float t = E[k] - A[k]; len2 = fmaf(t, t, len2); }
+    if (len2 > 0.f) {
+      float sb;
+      int ne;
+      const float fb = brent32(P, L, A, E, &sb, &ne);
+      evals += ne;
+      if (!(alc0 >= -fb)) { s_star = sb; alc_star = -fb; }
+    }
+    if (lane == 0) { L.ralc[i] = alc_star; L.rs[i] = s_star; L.rnev[i] = evals; }
+    __syncwarp();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int ib = 0, ev = 0;
+    for (int i = 1; i < R; ++i) if (L.ralc[i] > L.ralc[ib]) ib = i;
+    float second = -1.f;
+    for (int i = 0; i < R; ++i) { ev += L.rnev[i]; if (i != ib) second = fmaxf(second, L.ralc[i]); }
+    const float* A = L.rA + ib * PP;
+    const float* E = L.rE + ib * PP;
+    for (int k = 0; k < PP; ++k) L.xs[k] = fmaf(L.rs[ib], E[k] - A[k], A[k]);
+    L.dscal[1] = (L.ralc[ib] > 0.f && R > 1) ? (double)((L.ralc[ib] - second) / L.ralc[ib]) : 0.0;
+    L.ired[0] = ev;
+  }
+  __syncthreads();
+  // snap (FP32 distances; ties to the lower rank)
+  for (int pass = 0; pass < 2; ++pass) {
+    VI t; t.v = -__int_as_float(0x7f800000); t.v2 = t.v; t.i = -1;
+    for (int r = tid; r < nc; r += blockDim.x) {
+      if (L.used[r]) continue;
+      const float* c = cand_f(P, cl, r);
+      if (pass == 0) {
+        bool forbidden = false;
+        for (int i = 0; i < R; ++i) {
+          if (L.starts[i] != r) continue;
+          bool same = true;
+          for (int k = 0; k < PP; ++k) if (c[k] != L.xs[k]) same = false;
+          if (!same) forbidden = true;
+        }
+        if (forbidden) continue;
+      }
+      float d = 0.f;
+      for (int k = 0; k < PP; ++k) { float q = c[k] - L.xs[k]; d = fmaf(q, q, d); }
+      const float nd = -d;   // maximise -d
+      if (nd > t.v) { t.v2 = t.v; t.v = nd; t.i = r; }
+      else if (nd > t.v2) t.v2 = nd;
+    }
+    VI b = block_best(t, L.red, L.ired + 1);
+    if (b.i >= 0 || pass == 1) {
+      *gap_out = L.dscal[1];
+      *nev_out = L.ired[0];
+      return b.i;
+    }
+  }
+  return -1;
+}
+
+template <int SEARCH>
+__global__ void __launch_bounds__(D32_THREADS) design32(D32Params P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int64_t loc = blockIdx.x;
+  if (loc >= P.M) return;
+  const int tid = threadIdx.x, p = P.p, PP = P.PP, ld = P.n_max, R = P.R;
+  const int nc = P.nc_loc ? P.nc_loc[loc] : P.nc_max;
+  const int n = P.n_loc ? P.n_loc[loc] : P.n_max;
+  const int32_t* cl = P.cand + loc * P.nc_max;
+  double* Lg = P.Linv + loc * (int64_t)ld * ld;
+  float* Kc_loc = (SEARCH == 0) ? P.Kc + loc * (int64_t)ld * P.nc_max : nullptr;
+
+  L32 L;
+  L.ldf = ld | 1;
+  double* dp = reinterpret_cast<double*>(smem);
+  L.S64 = dp; dp += ld * p;
+  L.xq = dp; dp += p;
+  L.kvec = dp; dp += ld;
+  L.l = dp; dp += ld;
+  L.z = dp; dp += ld;
+  L.zy = dp; dp += ld;
+  L.kx = dp; dp += ld;
+  L.dred = dp; dp += 4 * D32_WARPS;
+  L.dscal = dp; dp += 4;
+  float* fp = reinterpret_cast<float*>(dp);
+  L.Lf = fp; fp += ld * L.ldf;
+  L.zf = fp; fp += ld;
+  L.Sf = fp; fp += ld * PP;
+  L.xf = fp; fp += PP;
+  L.lof = fp; fp += PP;
+  L.hif = fp; fp += PP;
+  L.kzf = fp; fp += (SEARCH == 0) ? exh_pass(ld) * L.ldf : D32_WARPS * ld;
+  L.rz = fp; fp += D32_WARPS * PP;
+  L.rA = fp; fp += R * PP;
+  L.rE = fp; fp += R * PP;
+  L.ralc = fp; fp += R;
+  L.rs = fp; fp += R;
+  L.xs = fp; fp += PP;
+  L.red = fp; fp += 4 * D32_WARPS;
+  int* ip = reinterpret_cast<int*>(fp);
+  L.sel = ip; ip += ld;
+  L.starts = ip; ip += R;
+  L.rnev = ip; ip += R;
+  L.ired = ip; ip += 2 * D32_WARPS + 2;
+  L.used = reinterpret_cast<unsigned char*>(ip);
+  L.j = 0;
+  L.neg_inv_theta = (float)(-1.0 / P.theta);
+  L.onepg = (float)(1.0 + P.g);
+
+  for (int r = tid; r < nc; r += blockDim.x) L.used[r] = 0;
+  if (tid < p) L.xq[tid] = P.xref[loc * p + tid];
+  if (tid < PP) {
+    const bool in = tid < p;
+    L.xf[tid] = in ? (float)(P.xref[loc * p + tid] - P.center[tid]) : 0.f;
+    L.lof[tid] = in ? (float)(P.lo[tid] - P.center[tid]) : 0.f;
+    L.hif[tid] = in ? (float)(P.hi[tid] - P.center[tid]) : 0.f;
+  }
+  for (int i = tid; i < ld * L.ldf; i += blockDim.x) L.Lf[i] = 0.f;
+  if (P.tie_gap) for (int i = tid; i < ld; i += blockDim.x) P.tie_gap[loc * ld + i] = 0.0;
+  if (P.nevals) for (int i = tid; i < ld; i += blockDim.x) P.nevals[loc * ld + i] = 0;
+  __syncthreads();
+
+  bool ok = (n >= P.n0) && (n <= nc) && (n <= ld);
+  for (int r = 0; r < P.n0 && ok; ++r) ok = add_point32<SEARCH>(P, L, cl, nc, r, Lg, Kc_loc);
+  for (int j = P.n0; j < n && ok; ++j) {
+    double gap = 0.0;
+    int ne = 0;
+    int r = (SEARCH == 0) ? search_exh32(P, L, cl, nc, Kc_loc, &gap)
+                          : search_ray32(P, L, cl, nc, &gap, &ne);
+    if (tid == 0) {
+      if (P.tie_gap) P.tie_gap[loc * ld + (j - P.n0)] = gap;
+      if (P.nevals) P.nevals[loc * ld + (j - P.n0)] = ne;
+    }
+    ok = (r >= 0) && add_point32<SEARCH>(P, L, cl, nc, r, Lg, Kc_loc);
+  }
+  if (ok) {
+    double a = 0.0, b = 0.0, c = 0.0, dmy = 0.0;
+    for (int i = tid; i < L.j; i += blockDim.x) {
+      a = fma(L.z[i], L.zy[i], a);
+      b = fma(L.zy[i], L.zy[i], b);
+      c = fma(L.z[i], L.z[i], c);
+    }
+    block_sum2(a, b, L.dred);
+    block_sum2(c, dmy, L.dred);
+    if (tid == 0) {
+      P.mean[loc] = a;
+      P.s2[loc] = b * ((1.0 + P.g) - c) / (double)L.j;
+    }
+  } else if (tid == 0) {
+    P.mean[loc] = __longlong_as_double(0x7ff8000000000000ll);
+    P.s2[loc] = __longlong_as_double(0x7ff8000000000000ll);
+    atomicOr(P.status, LAGP_DEV_BAD_UPDATE);
+  }
+  if (P.selected)
+    for (int i = tid; i < ld; i += blockDim.x)
+      P.selected[loc * ld + i] = (i < L.j) ? cl[L.sel[i]] : -1;
+}
+
+static size_t smem_design32(int n_max, int p, int PP, int nc_max, int R, int search) {
+  const int ldf = n_max | 1;
+  size_t d = (size_t)n_max * p + p + 5 * n_max + 4 * D32_WARPS + 4;
+  size_t f = (size_t)n_max * ldf + n_max + (size_t)n_max * PP + 3 * PP +
+             (search == 0 ? (size_t)exh_pass(n_max) * ldf : (size_t)D32_WARPS * n_max) + D32_WARPS * PP +
+             2 * R * PP + 2 * R + PP + 4 * D32_WARPS;
+  size_t i = (size_t)n_max + 2 * R + 2 * D32_WARPS + 2;
+  return d * 8 + f * 4 + i * 4 + nc_max + 16;
+}
+
+cudaError_t launch_design_fp32(const DesignArgs& a, int search, cudaStream_t s) {
+  D32Params P;
+  P.X = a.X; P.Y = a.Y; P.p = a.p; P.PP = a.PP; P.Xf = a.ws->Xf; P.xref = a.xref; P.M = a.M;
+  P.cand = a.cand; P.nc_max = a.nc_max; P.nc_loc = a.nc_loc; P.n0 = a.n0; P.n_max = a.n_max;
+  P.n_loc = a.n_loc; P.theta = a.theta; P.g = a.g; P.R = a.nrays; P.lo = a.ws->lo;
+  P.hi = a.ws->hi; P.center = a.ws->center; P.mean = a.mean; P.s2 = a.s2;
+  P.selected = a.selected; P.tie_gap = a.tie_gap; P.nevals = a.nevals; P.Linv = a.ws->state64;
+  P.Kc = a.ws->state32; P.status = a.ws->status;
+  size_t sm = smem_design32(a.n_max, a.p, a.PP, a.nc_max, a.nrays, search);
+  cudaError_t err;
+  if (search == 0) {
+    err = cudaFuncSetAttribute(design32<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (err != cudaSuccess) return err;
+    prof_begin("design32_exhaustive", s);
+    design32<0><<<(unsigned)a.M, D32_THREADS, sm, s>>>(P);
+    prof_end(s);
+  } else {
+    err = cudaFuncSetAttribute(design32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (err != cudaSuccess) return err;
+    prof_begin("design32_ray", s);
+    design32<1><<<(unsigned)a.M, D32_THREADS, sm, s>>>(P);
+    prof_end(s);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace lagp

@@ -1,0 +1,444 @@
+// knn.cu -- brute-force tiled kNN candidate selection (Gramacy & Haaland,
+// Sec 2.2: the local search is restricted to the N' nearest neighbours of x).
+//
+// Two stages:
+//  1. knn_stream: each CTA owns 32 predictive locations (4 per warp) and
+//     streams the whole design through shared memory in 256-point tiles moved
+//     by bulk-copy (TMA) into a double buffer.  Distances are computed in FP32
+//     from centred coordinates; a point enters its location's candidate
+//     buffer when d32 <= tau + 2 err, where tau is the N'-th smallest buffered
+//     d32 and err a proven bound on |d32 - d64|.  A warp radix-selects tau and
+//     compacts the buffer whenever the next tile might overflow it.
+//  2. knn_rank: one CTA per location computes the exact binary64 distances of
+//     the surviving points in the oracle's operation order and bitonic-sorts
+//     (d64, index) pairs; the first N' indices are the candidate list.
+// Every true member of the N'-nearest set survives stage 1: at the end at
+// least N' points have d32 <= tau, so the N'-th smallest d64 is at most
+// tau + err, and any member has d32 <= d64 + err <= tau + 2 err.
+#include <cfloat>
+#include <cstdint>
+
+#include "common.cuh"
+#include "lagp_internal.h"
+
+namespace lagp {
+
+#define KNN_WARPS 8
+#define KNN_QW 4   // locations per warp
+
+struct __align__(8) KnnEntry {
+  float d;
+  int32_t idx;
+};
+
+// ---------------------------------------------------------------------------
+// Preparation: bounding box (exact min/max), centred FP32 copy of the design,
+// squared norms, largest squared norm.
+// ---------------------------------------------------------------------------
+__global__ void bbox_partial(const double* __restrict__ X, int64_t N, int p,
+                             double* __restrict__ part /*[gridDim.x][2p]*/) {
+  __shared__ double slo[256], shi[256];
+  for (int k = 0; k < p; ++k) {
+    double lo = __longlong_as_double(0x7ff0000000000000ll), hi = -lo;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      double v = X[i * p + k];
+      lo = fmin(lo, v);
+      hi = fmax(hi, v);
+    }
+    slo[threadIdx.x] = lo;
+    shi[threadIdx.x] = hi;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) {
+        slo[threadIdx.x] = fmin(slo[threadIdx.x], slo[threadIdx.x + s]);
+        shi[threadIdx.x] = fmax(shi[threadIdx.x], shi[threadIdx.x + s]);
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      part[blockIdx.x * 2 * p + k] = slo[0];
+      part[blockIdx.x * 2 * p + p + k] = shi[0];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void bbox_final(const double* __restrict__ part, int nparts, int p,
+                           double* __restrict__ lo, double* __restrict__ hi,
+                           double* __restrict__ center) {
+  int k = threadIdx.x;
+  if (k >= p) return;
+  double l = part[k], h = part[p + k];
+  for (int b = 1; b < nparts; ++b) {
+    l = fmin(l, part[b * 2 * p + k]);
+    h = fmax(h, part[b * 2 * p + p + k]);
+  }
+  lo[k] = l;
+  hi[k] = h;
+  center[k] = 0.5 * (l + h);
+}
+
+// Xf[i][0..PP) = fl32(X[i] - center) (zero padded), nx[i] = |Xf[i]|^2 in FP32;
+// rows N..Npad-1 are zero.  maxn2 receives max_i nx[i] (as ordered bits).
+__global__ void design_to_f32(const double* __restrict__ X, int64_t N, int64_t Npad, int p, int PP,
+                              const double* __restrict__ center, float* __restrict__ Xf,
+                              float* __restrict__ nx, unsigned* __restrict__ maxn2_bits) {
+  float local_max = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Npad;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (int k = 0; k < PP; ++k) {
+      float v = 0.f;
+      if (i < N && k < p) v = (float)(X[i * p + k] - center[k]);
+      Xf[i * PP + k] = v;
+      acc = fmaf(v, v, acc);
+    }
+    nx[i] = acc;
+    local_max = fmaxf(local_max, acc);
+  }
+  for (int o = 16; o > 0; o >>= 1) local_max = fmaxf(local_max, __shfl_xor_sync(0xffffffffu, local_max, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(maxn2_bits, __float_as_uint(local_max));
+}
+
+// ---------------------------------------------------------------------------
+// Warp radix select: the k-th smallest (1-based) of cnt non-negative float
+// keys in e[0..cnt), returned as its bit pattern.  hist: 256 words of this
+// warp's shared memory.
+// ---------------------------------------------------------------------------
+__device__ uint32_t warp_select_kth(const KnnEntry* e, int cnt, int k, uint32_t* hist) {
+  const int lane = threadIdx.x & 31;
+  uint32_t prefix = 0, pmask = 0;
+  int kk = k;
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    for (int b = lane; b < 256; b += 32) hist[b] = 0;
+    __syncwarp();
+    for (int i = lane; i < cnt; i += 32) {
+      uint32_t key = __float_as_uint(e[i].d);
+      if ((key & pmask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+    }
+    __syncwarp();
+    // lane owns bins 8*lane .. 8*lane+7
+    uint32_t c[8], tot = 0;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) { c[b] = hist[lane * 8 + b]; tot += c[b]; }
+    uint32_t incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    uint32_t excl = incl - tot;
+    // the lane whose range holds the kk-th key finds the digit
+    int found = ((int)excl < kk && (int)incl >= kk);
+    uint32_t fmask = __ballot_sync(0xffffffffu, found);
+    int src = __ffs(fmask) - 1;
+    uint32_t digit = 0;
+    int kk_new = kk;
+    if (lane == src) {
+      uint32_t run = excl;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        if ((int)(run + c[b]) >= kk) { digit = lane * 8 + b; kk_new = kk - (int)run; break; }
+        run += c[b];
+      }
+    }
+    digit = __shfl_sync(0xffffffffu, digit, src < 0 ? 0 : src);
+    kk = __shfl_sync(0xffffffffu, kk_new, src < 0 ? 0 : src);
+    prefix |= digit << shift;
+    pmask |= 255u << shift;
+    __syncwarp();
+  }
+  return prefix;
+}
+
+// Keep entries with d <= keep (stable, in place); returns the new count.
+__device__ int warp_compact(KnnEntry* e, int cnt, float keep) {
+  const int lane = threadIdx.x & 31;
+  int out = 0;
+  for (int base = 0; base < cnt; base += 32) {
+    int i = base + lane;
+    KnnEntry v;
+    bool ok = false;
+    if (i < cnt) { v = e[i]; ok = v.d <= keep; }
+    __syncwarp();
+    uint32_t m = __ballot_sync(0xffffffffu, ok);
+    if (ok) e[out + __popc(m & ((1u << lane) - 1u))] = v;
+    out += __popc(m);
+    __syncwarp();
+  }
+  return out;
+}
+
+template <int PP>
+__global__ void __launch_bounds__(KNN_WARPS * 32)
+knn_stream(const float* __restrict__ Xf, const float* __restrict__ nx, int64_t N, int64_t ntiles,
+           int p, const double* __restrict__ xref, int64_t M, const double* __restrict__ center,
+           const unsigned* __restrict__ maxn2_bits, int nc_max, const int32_t* __restrict__ nc_loc,
+           int cap, KnnEntry* __restrict__ buf, int32_t* __restrict__ cnt_out,
+           unsigned* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  float* tile = reinterpret_cast<float*>(smem);                    // [2][TILE][PP]
+  float* tnorm = tile + 2 * LAGP_KNN_TILE * PP;                     // [2][TILE]
+  uint32_t* hist = reinterpret_cast<uint32_t*>(tnorm + 2 * LAGP_KNN_TILE);  // [WARPS][256]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(hist + KNN_WARPS * 256);      // [2]
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t q0 = (int64_t)blockIdx.x * (KNN_WARPS * KNN_QW) + warp * KNN_QW;
+
+  // per-location state (warp-uniform)
+  float qf[KNN_QW][PP], nq[KNN_QW], err[KNN_QW], keep[KNN_QW];
+  int cnt[KNN_QW], ncq[KNN_QW];
+  bool live[KNN_QW];
+  const float rmax = sqrtf(__uint_as_float(*maxn2_bits)) * 1.0001f;
+#pragma unroll
+  for (int a = 0; a < KNN_QW; ++a) {
+    int64_t q = q0 + a;
+    live[a] = q < M;
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < PP; ++k) {
+      float v = 0.f;
+      if (live[a] && k < p) v = (float)(xref[q * p + k] - center[k]);
+      qf[a][k] = v;
+      acc = fmaf(v, v, acc);
+    }
+    nq[a] = acc;
+    float r = rmax + sqrtf(acc) * 1.0001f;
+    // |d32 - d64| <= (p + 12) 2^-24 (|a| + |b|)^2, with a 25% margin
+    err[a] = (float)(p + 12) * 0x1p-24f * 1.25f * r * r;
+    keep[a] = __int_as_float(0x7f800000);
+    cnt[a] = 0;
+    ncq[a] = live[a] ? (nc_loc ? nc_loc[q] : nc_max) : 0;
+  }
+
+  const uint32_t tile_bytes = LAGP_KNN_TILE * PP * sizeof(float);
+  const uint32_t norm_bytes = LAGP_KNN_TILE * sizeof(float);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 2 && s < ntiles; ++s) {
+      mbar_expect_tx(&bar[s], tile_bytes + norm_bytes);
+      bulk_g2s(tile + s * LAGP_KNN_TILE * PP, Xf + (int64_t)s * LAGP_KNN_TILE * PP, tile_bytes, &bar[s]);
+      bulk_g2s(tnorm + s * LAGP_KNN_TILE, nx + (int64_t)s * LAGP_KNN_TILE, norm_bytes, &bar[s]);
+    }
+  }
+
+  bool timed_out = false;
+  for (int64_t t = 0; t < ntiles; ++t) {
+    const int st = (int)(t & 1);
+    if (!mbar_wait(&bar[st], (uint32_t)((t >> 1) & 1))) {
+      timed_out = true;
+    }
+    if (__syncthreads_or(timed_out)) {
+      if (threadIdx.x == 0) {
+        atomicOr(status, LAGP_DEV_TIMEOUT);
+        // drain the copies still in flight into this CTA's buffers (bounded)
+        mbar_wait(&bar[st], (uint32_t)((t >> 1) & 1));
+        if (t + 1 < ntiles) mbar_wait(&bar[st ^ 1], (uint32_t)(((t + 1) >> 1) & 1));
+      }
+      __syncthreads();
+      break;
+    }
+    const float* T = tile + st * LAGP_KNN_TILE * PP;
+    const float* TN = tnorm + st * LAGP_KNN_TILE;
+    const int64_t base = t * LAGP_KNN_TILE;
+#pragma unroll 1
+    for (int s = 0; s < LAGP_KNN_TILE / 32; ++s) {
+      const int pt = s * 32 + lane;
+      const int64_t gi = base + pt;
+      float xv[PP];
+#pragma unroll
+      for (int k = 0; k < PP; k += 4) {
+        float4 v4 = *reinterpret_cast<const float4*>(T + pt * PP + k);
+        xv[k] = v4.x; xv[k + 1] = v4.y; xv[k + 2] = v4.z; xv[k + 3] = v4.w;
+      }
+      const float nxp = TN[pt];
+      const bool valid = gi < N;
+#pragma unroll
+      for (int a = 0; a < KNN_QW; ++a) {
+        float dot = 0.f;
+#pragma unroll
+        for (int k = 0; k < PP; ++k) dot = fmaf(qf[a][k], xv[k], dot);
+        float d = fmaxf(fmaf(-2.f, dot, nq[a] + nxp), 0.f);
+        bool pass = live[a] && valid && d <= keep[a];
+        uint32_t m = __ballot_sync(0xffffffffu, pass);
+        if (m) {
+          int pos = cnt[a] + __popc(m & ((1u << lane) - 1u));
+          if (pass && pos < cap) {
+            KnnEntry e; e.d = d; e.idx = (int32_t)gi;
+            buf[(q0 + a) * (int64_t)cap + pos] = e;
+          }
+          cnt[a] += __popc(m);
+        }
+      }
+    }
+    // compact any buffer that the next tile could overflow
+#pragma unroll
+    for (int a = 0; a < KNN_QW; ++a) {
+      if (live[a] && cnt[a] > cap - LAGP_KNN_TILE) {
+        KnnEntry* e = buf + (q0 + a) * (int64_t)cap;
+        int c = min(cnt[a], cap);
+        if (cnt[a] > cap) atomicOr(status, LAGP_DEV_KNN_OVERFLOW);
+        __syncwarp();
+        uint32_t kb = warp_select_kth(e, c, ncq[a], hist + warp * 256);
+        float kth = __uint_as_float(kb);
+        keep[a] = __fadd_ru(kth, 2.f * err[a]);
+        cnt[a] = warp_compact(e, c, keep[a]);
+        if (cnt[a] > cap - LAGP_KNN_TILE && lane == 0) atomicOr(status, LAGP_DEV_KNN_OVERFLOW);
+      }
+    }
+    __syncthreads();  // every warp is done with stage st
+    if (threadIdx.x == 0 && t + 2 < ntiles) {
+      mbar_expect_tx(&bar[st], tile_bytes + norm_bytes);
+      bulk_g2s(tile + st * LAGP_KNN_TILE * PP, Xf + (t + 2) * LAGP_KNN_TILE * PP, tile_bytes, &bar[st]);
+      bulk_g2s(tnorm + st * LAGP_KNN_TILE, nx + (t + 2) * LAGP_KNN_TILE, norm_bytes, &bar[st]);
+    }
+  }
+  // final: keep d32 <= (N'-th smallest) + 2 err
+#pragma unroll
+  for (int a = 0; a < KNN_QW; ++a) {
+    if (!live[a]) continue;
+    KnnEntry* e = buf + (q0 + a) * (int64_t)cap;
+    int c = min(cnt[a], cap);
+    __syncwarp();
+    if (c >= ncq[a] && ncq[a] > 0) {
+      uint32_t kb = warp_select_kth(e, c, ncq[a], hist + warp * 256);
+      c = warp_compact(e, c, __fadd_ru(__uint_as_float(kb), 2.f * err[a]));
+    }
+    if (lane == 0) cnt_out[q0 + a] = timed_out ? 0 : c;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Exact ranking: binary64 distances in the oracle's order, bitonic sort of
+// (d64, index), first N' indices out.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+knn_rank(const double* __restrict__ X, int p, const double* __restrict__ xref, int64_t M,
+         int nc_max, const int32_t* __restrict__ nc_loc, int cap,
+         const KnnEntry* __restrict__ buf, const int32_t* __restrict__ cnt,
+         int32_t* __restrict__ cand /*[M][nc_max]*/, unsigned* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char smem_rank[];
+  const int64_t q = blockIdx.x;
+  if (q >= M) return;
+  const int c = cnt[q];
+  const int nc = nc_loc ? nc_loc[q] : nc_max;
+  double* key = reinterpret_cast<double*>(smem_rank);
+  int32_t* idx = reinterpret_cast<int32_t*>(key + cap);
+  __shared__ double xq[LAGP_MAX_P];
+  if (threadIdx.x < p) xq[threadIdx.x] = xref[q * p + threadIdx.x];
+  int sz = 1;
+  while (sz < c) sz <<= 1;
+  __syncthreads();
+  const KnnEntry* e = buf + q * (int64_t)cap;
+  for (int i = threadIdx.x; i < sz; i += blockDim.x) {
+    if (i < c) {
+      int32_t gi = e[i].idx;
+      key[i] = sqdist64(X + (int64_t)gi * p, xq, p);
+      idx[i] = gi;
+    } else {
+      key[i] = __longlong_as_double(0x7ff0000000000000ll);
+      idx[i] = 0x7fffffff;
+    }
+  }
+  __syncthreads();
+  for (int k = 2; k <= sz; k <<= 1) {
+    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+      for (int i = threadIdx.x; i < sz; i += blockDim.x) {
+        int l = i ^ jj;
+        if (l > i) {
+          bool up = (i & k) == 0;
+          double ki = key[i], kl = key[l];
+          int32_t ii = idx[i], il = idx[l];
+          bool gt = (ki > kl) || (ki == kl && ii > il);
+          if (gt == up) {
+            key[i] = kl; key[l] = ki;
+            idx[i] = il; idx[l] = ii;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (c < nc && threadIdx.x == 0) atomicOr(status, LAGP_DEV_KNN_OVERFLOW);
+  for (int r = threadIdx.x; r < nc_max; r += blockDim.x)
+    cand[q * nc_max + r] = (r < nc && r < c) ? idx[r] : -1;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers.
+// ---------------------------------------------------------------------------
+size_t knn_smem_stream(int PP) {
+  return (size_t)2 * LAGP_KNN_TILE * PP * 4 + 2 * LAGP_KNN_TILE * 4 + KNN_WARPS * 256 * 4 + 16;
+}
+
+int knn_cap(int nc_max) {
+  int cap = 512;
+  while (cap < 2 * nc_max) cap <<= 1;
+  return cap;
+}
+
+cudaError_t launch_prepare(const double* X, int64_t N, int p, int PP, int64_t Npad,
+                           const Workspace& ws, cudaStream_t s) {
+  const int parts = 64;
+  prof_begin("bbox_partial", s);
+  bbox_partial<<<parts, 256, 0, s>>>(X, N, p, ws.bbox_part);
+  prof_end(s);
+  prof_begin("bbox_final", s);
+  bbox_final<<<1, 32, 0, s>>>(ws.bbox_part, parts, p, ws.lo, ws.hi, ws.center);
+  prof_end(s);
+  cudaMemsetAsync(ws.maxn2, 0, sizeof(unsigned), s);
+  prof_begin("design_to_f32", s);
+  design_to_f32<<<1216, 256, 0, s>>>(X, N, Npad, p, PP, ws.center, ws.Xf, ws.nx, ws.maxn2);
+  prof_end(s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_knn(const double* X, int64_t N, int p, int PP, int64_t Npad,
+                       const double* xref, int64_t M, int nc_max, const int32_t* nc_loc,
+                       int32_t* cand, const Workspace& ws, cudaStream_t s) {
+  const int cap = knn_cap(nc_max);
+  const int64_t ntiles = Npad / LAGP_KNN_TILE;
+  const int qpb = KNN_WARPS * KNN_QW;
+  dim3 grid((unsigned)((M + qpb - 1) / qpb));
+  size_t sm = knn_smem_stream(PP);
+  cudaError_t err;
+  switch (PP) {
+#define KNN_CASE(V)                                                                        \
+  case V:                                                                                  \
+    err = cudaFuncSetAttribute(knn_stream<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                               (int)sm);                                                   \
+    if (err != cudaSuccess) return err;                                                    \
+    prof_begin("knn_stream", s);                                                           \
+    knn_stream<V><<<grid, KNN_WARPS * 32, sm, s>>>(ws.Xf, ws.nx, N, ntiles, p, xref, M,    \
+                                                   ws.center, ws.maxn2, nc_max, nc_loc,    \
+                                                   cap, reinterpret_cast<KnnEntry*>(       \
+                                                            ws.knn_buf),                   \
+                                                   ws.knn_cnt, ws.status);                 \
+    prof_end(s);                                                                           \
+    break;
+    KNN_CASE(4)
+    KNN_CASE(8)
+    KNN_CASE(12)
+    KNN_CASE(16)
+#undef KNN_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  size_t smr = (size_t)cap * (8 + 4);
+  err = cudaFuncSetAttribute(knn_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+  if (err != cudaSuccess) return err;
+  prof_begin("knn_rank", s);
+  knn_rank<<<(unsigned)M, 256, smr, s>>>(X, p, xref, M, nc_max, nc_loc, cap,
+                                         reinterpret_cast<const KnnEntry*>(ws.knn_buf),
+                                         ws.knn_cnt, cand, ws.status);
+  prof_end(s);
+  return cudaGetLastError();
+}
+
+}  // namespace lagp

@@ -1,0 +1,219 @@
+"""ctypes binding of the C ABI in include/lagp.h (liblagp_gb300.so).
+
+Argument marshalling only: every step of local approximate GP prediction runs
+in the CUDA kernels of the library.  PyTorch supplies device memory and
+streams.  The binding refuses to run without the compiled library; there is no
+CPU fallback.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblagp_gb300.so")
+
+LAGP_EXHAUSTIVE, LAGP_RAY = 0, 1
+LAGP_FP64, LAGP_FP32_SCORE = 0, 1
+SEARCH = {"exhaustive": LAGP_EXHAUSTIVE, "ray": LAGP_RAY}
+PRECISION = {"fp64": LAGP_FP64, "fp32": LAGP_FP32_SCORE}
+ERRORS = {-1: "invalid argument", -2: "workspace too small", -3: "CUDA error",
+          -4: "device reported a failure"}
+STATUS_BITS = {1: "timeout", 2: "kNN tie capacity", 4: "numeric (v <= 0)"}
+
+EXPORTED = ("laGP_workspace_bytes", "laGP_build_and_predict", "laGP_knn_workspace_bytes",
+            "laGP_knn", "laGP_status", "laGP_host_workspace_bytes",
+            "laGP_build_and_predict_host", "laGP_profile", "laGP_profile_read")
+
+_lib = None
+
+
+class LagpError(RuntimeError):
+    def __init__(self, fn, rc, status=0):
+        bits = [v for k, v in STATUS_BITS.items() if status & k]
+        super().__init__("%s failed: %s (%d)%s" % (fn, ERRORS.get(rc, "error"), rc,
+                                                   (" status: " + ", ".join(bits)) if bits else ""))
+        self.rc, self.status = rc, status
+
+
+def load():
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("liblagp_gb300.so is not built: run __graft_entry__.build() or "
+                           "python paper_1409_0074_gb300/build.py")
+    lib = C.CDLL(LIB_PATH)
+    i64, i32, vp, sz, dbl = C.c_int64, C.c_int, C.c_void_p, C.c_size_t, C.c_double
+    lib.laGP_workspace_bytes.restype = sz
+    lib.laGP_workspace_bytes.argtypes = [i64, i32, i64, i32, i32, i32, i32, i32]
+    lib.laGP_host_workspace_bytes.restype = sz
+    lib.laGP_host_workspace_bytes.argtypes = [i64, i32, i64, i32, i32, i32, i32, i32]
+    lib.laGP_knn_workspace_bytes.restype = sz
+    lib.laGP_knn_workspace_bytes.argtypes = [i64, i32, i64, i32]
+    full = [vp, vp, i64, i32, vp, i64, i32, i32, i32, dbl, dbl, i32, i32, i32, vp, vp, vp, vp,
+            vp, vp, vp, vp, sz, vp]
+    lib.laGP_build_and_predict.restype = i32
+    lib.laGP_build_and_predict.argtypes = full
+    lib.laGP_build_and_predict_host.restype = i32
+    lib.laGP_build_and_predict_host.argtypes = full
+    lib.laGP_knn.restype = i32
+    lib.laGP_knn.argtypes = [vp, i64, i32, vp, i64, i32, vp, vp, sz, vp]
+    lib.laGP_status.restype = i32
+    lib.laGP_status.argtypes = [vp, vp, C.POINTER(C.c_uint)]
+    lib.laGP_profile.restype = i32
+    lib.laGP_profile.argtypes = [i32]
+    lib.laGP_profile_read.restype = i32
+    lib.laGP_profile_read.argtypes = [i32, C.c_char_p, C.POINTER(C.c_double),
+                                      C.POINTER(C.c_int32)]
+    _lib = lib
+    return lib
+
+
+def _ptr(t, dtype=None, n=None):
+    """Device pointer of a contiguous CUDA tensor (or None)."""
+    if t is None:
+        return None
+    import torch
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError("expected dtype %s, got %s" % (dtype, t.dtype))
+    if n is not None and t.numel() < n:
+        raise ValueError("tensor too small: %d < %d" % (t.numel(), n))
+    return t.data_ptr()
+
+
+def _hptr(a, dtype, n=None):
+    if a is None:
+        return None
+    if not (isinstance(a, np.ndarray) and a.dtype == dtype and a.flags.c_contiguous):
+        raise ValueError("expected a C-contiguous numpy array of %s" % dtype)
+    if n is not None and a.size < n:
+        raise ValueError("array too small")
+    return a.ctypes.data
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _check(name, rc):
+    if rc != 0:
+        raise LagpError(name, rc)
+
+
+def laGP_workspace_bytes(N, p, M, n, N_close, nrays, search, precision):
+    return load().laGP_workspace_bytes(N, p, M, n, N_close, nrays, search, precision)
+
+
+def laGP_host_workspace_bytes(N, p, M, n, N_close, nrays, search, precision):
+    return load().laGP_host_workspace_bytes(N, p, M, n, N_close, nrays, search, precision)
+
+
+def laGP_knn_workspace_bytes(N, p, M, N_close):
+    return load().laGP_knn_workspace_bytes(N, p, M, N_close)
+
+
+def laGP_build_and_predict(design, y, xref, n0, n, N_close, theta, g, search, nrays, precision,
+                           mean, s2, workspace, n_loc=None, nclose_loc=None, selected=None,
+                           tie_gap=None, nevals=None, stream=None):
+    """Enqueue the whole path on `stream` (torch tensors on the GPU)."""
+    import torch
+    N, p = design.shape
+    M = xref.shape[0]
+    lib = load()
+    rc = lib.laGP_build_and_predict(
+        _ptr(design, torch.float64), _ptr(y, torch.float64, N), N, p, _ptr(xref, torch.float64),
+        M, n0, n, N_close, float(theta), float(g), search, nrays, precision,
+        _ptr(n_loc, torch.int32, M), _ptr(nclose_loc, torch.int32, M),
+        _ptr(mean, torch.float64, M), _ptr(s2, torch.float64, M),
+        _ptr(selected, torch.int32, M * n), _ptr(tie_gap, torch.float64, M * n),
+        _ptr(nevals, torch.int32, M * n), _ptr(workspace), workspace.numel() * workspace.element_size(),
+        _stream(stream))
+    _check("laGP_build_and_predict", rc)
+
+
+def laGP_knn(design, xref, N_close, cand, workspace, stream=None):
+    import torch
+    N, p = design.shape
+    M = xref.shape[0]
+    rc = load().laGP_knn(_ptr(design, torch.float64), N, p, _ptr(xref, torch.float64), M,
+                         N_close, _ptr(cand, torch.int32, M * N_close), _ptr(workspace),
+                         workspace.numel() * workspace.element_size(), _stream(stream))
+    _check("laGP_knn", rc)
+
+
+def laGP_status(workspace, stream=None):
+    st = C.c_uint(0)
+    rc = load().laGP_status(_ptr(workspace), _stream(stream), C.byref(st))
+    return rc, st.value
+
+
+def laGP_profile(enable):
+    _check("laGP_profile", load().laGP_profile(1 if enable else 0))
+
+
+def laGP_profile_read(max_kernels=32):
+    """{kernel name: (total ms, launches)} of the events recorded since laGP_profile(1)."""
+    names = C.create_string_buffer(32 * max_kernels)
+    ms = (C.c_double * max_kernels)()
+    cnt = (C.c_int32 * max_kernels)()
+    k = load().laGP_profile_read(max_kernels, names, ms, cnt)
+    if k < 0:
+        raise LagpError("laGP_profile_read", k)
+    raw = names.raw
+    out = {}
+    for i in range(k):
+        nm = raw[32 * i: 32 * i + 32].split(b"\0", 1)[0].decode()
+        out[nm] = (ms[i], cnt[i])
+    return out
+
+
+def laGP_build_and_predict_host(design, y, xref, n0, n, N_close, theta, g, search, nrays,
+                                precision, mean, s2, workspace, n_loc=None, nclose_loc=None,
+                                selected=None, tie_gap=None, nevals=None, stream=None):
+    """Host-buffer form (numpy arrays; pinned memory recommended)."""
+    N, p = design.shape
+    M = xref.shape[0]
+    rc = load().laGP_build_and_predict_host(
+        _hptr(design, np.float64), _hptr(y, np.float64, N), N, p, _hptr(xref, np.float64), M, n0,
+        n, N_close, float(theta), float(g), search, nrays, precision,
+        _hptr(n_loc, np.int32, M), _hptr(nclose_loc, np.int32, M), _hptr(mean, np.float64, M),
+        _hptr(s2, np.float64, M), _hptr(selected, np.int32, M * n),
+        _hptr(tie_gap, np.float64, M * n), _hptr(nevals, np.int32, M * n), _ptr(workspace),
+        workspace.numel() * workspace.element_size(), _stream(stream))
+    _check("laGP_build_and_predict_host", rc)
+
+
+def predict(design, y, xref, n0, n, N_close, theta, g, search="ray", nrays=0, precision="fp32",
+            n_loc=None, nclose_loc=None, want_trace=False, stream=None):
+    """Convenience wrapper: allocates outputs and workspace with torch, enqueues
+    the path, checks the device status.  Returns a dict of CUDA tensors."""
+    import torch
+    dev = design.device
+    M = xref.shape[0]
+    N, p = design.shape
+    s, pr = SEARCH[search], PRECISION[precision]
+    wsb = laGP_workspace_bytes(N, p, M, n, N_close, nrays, s, pr)
+    if wsb == 0:
+        raise LagpError("laGP_workspace_bytes", -1)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    out = dict(mean=torch.empty(M, dtype=torch.float64, device=dev),
+               s2=torch.empty(M, dtype=torch.float64, device=dev))
+    if want_trace:
+        out["selected"] = torch.empty((M, n), dtype=torch.int32, device=dev)
+        out["tie_gap"] = torch.empty((M, n), dtype=torch.float64, device=dev)
+        out["nevals"] = torch.empty((M, n), dtype=torch.int32, device=dev)
+    laGP_build_and_predict(design, y, xref, n0, n, N_close, theta, g, s, nrays, pr, out["mean"],
+                           out["s2"], ws, n_loc=n_loc, nclose_loc=nclose_loc,
+                           selected=out.get("selected"), tie_gap=out.get("tie_gap"),
+                           nevals=out.get("nevals"), stream=stream)
+    rc, st = laGP_status(ws, stream)
+    if rc != 0:
+        raise LagpError("laGP_build_and_predict (device)", rc, st)
+    return out

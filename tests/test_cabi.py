@@ -1,0 +1,85 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/lagp.h declares; host-side argument checks work without a GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lagp.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(laGP_\w+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1409_0074_gb300 import build
+    build.build()
+    from paper_1409_0074_gb300 import lagp
+    return lagp.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 7
+    for name in names:
+        assert hasattr(lib, name), name
+    from paper_1409_0074_gb300 import lagp
+    assert set(lagp.EXPORTED) <= set(names)
+
+
+def test_workspace_sizes_and_argument_checks(lib):
+    from paper_1409_0074_gb300 import lagp
+    ok = lagp.laGP_workspace_bytes(100000, 4, 10000, 50, 1000, 4, lagp.LAGP_RAY, lagp.LAGP_FP64)
+    assert ok > 0
+    # exhaustive FP64 keeps a correlation cache: larger
+    ex = lagp.laGP_workspace_bytes(100000, 4, 10000, 50, 1000, 4, lagp.LAGP_EXHAUSTIVE,
+                                   lagp.LAGP_FP64)
+    assert ex > ok
+    bad = [
+        (100000, 0, 10, 50, 1000, 4, 1, 0),      # p < 1
+        (100000, 17, 10, 50, 1000, 4, 1, 0),     # p > 16
+        (100000, 4, 10, 50, 40, 4, 1, 0),        # n > N_close
+        (500, 4, 10, 50, 1000, 4, 1, 0),         # N_close > N
+        (100000, 4, 10, 129, 1000, 4, 1, 0),     # n > 128
+        (100000, 4, 10, 50, 1000, 17, 1, 0),     # too many rays
+        (100000, 4, 10, 50, 52, 4, 1, 0),        # nrays > N_close - n
+        (100000, 4, 10, 50, 1000, 4, 2, 0),      # bad search
+        (100000, 4, 10, 50, 1000, 4, 1, 2),      # bad precision
+    ]
+    for args in bad:
+        assert lagp.laGP_workspace_bytes(*args) == 0, args
+    assert lagp.laGP_knn_workspace_bytes(1000, 3, 10, 1) > 0
+    assert lagp.laGP_host_workspace_bytes(1000, 3, 10, 10, 100, 2, 1, 1) > \
+        lagp.laGP_workspace_bytes(1000, 3, 10, 10, 100, 2, 1, 1)
+
+
+def test_invalid_calls_return_before_touching_the_device(lib):
+    vp = C.c_void_p
+    f = lib.laGP_build_and_predict
+    f.restype = C.c_int
+    f.argtypes = [vp, vp, C.c_int64, C.c_int, vp, C.c_int64, C.c_int, C.c_int, C.c_int,
+                  C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, vp, vp, vp,
+                  vp, C.c_size_t, vp]
+    fake = 4096
+    common = [fake, fake, 1000, 2, fake, 10]
+    # theta <= 0
+    assert f(*common, 3, 10, 100, 0.0, 1e-6, 0, 2, 0, None, None, fake, fake, None, None, None,
+             fake, 1 << 30, None) == -1
+    # n0 > n
+    assert f(*common, 11, 10, 100, 0.1, 1e-6, 0, 2, 0, None, None, fake, fake, None, None, None,
+             fake, 1 << 30, None) == -1
+    # null output
+    assert f(*common, 3, 10, 100, 0.1, 1e-6, 0, 2, 0, None, None, None, fake, None, None, None,
+             fake, 1 << 30, None) == -1
+    # workspace too small
+    assert f(*common, 3, 10, 100, 0.1, 1e-6, 0, 2, 0, None, None, fake, fake, None, None, None,
+             fake, 16, None) == -2
+    # M == 0 is a no-op
+    assert f(fake, fake, 1000, 2, fake, 0, 3, 10, 100, 0.1, 1e-6, 0, 2, 0, None, None, fake, fake,
+             None, None, None, fake, 1 << 30, None) == 0

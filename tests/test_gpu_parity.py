@@ -1,0 +1,264 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+FP64 form: the selected-index sequences must equal the oracle's, except at a
+step the oracle logged as a near-tie (relative gap below 1e-12), after which
+that location is excused; mean and s2 of the other locations within 1e-10
+relative.  (The kernels follow the oracle's operation order, so in practice
+every location is bit-identical; the tests report that count.)
+FP32-scoring form: s2 within 1e-4 relative at locations whose design equals
+the oracle's, and out-of-sample RMSE within 1% of the oracle's.
+kNN: candidate lists bit-exact (indices are integers).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1409_0074_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TIE_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def lagp(cuda):
+    from paper_1409_0074_gb300 import build
+    build.build()
+    from paper_1409_0074_gb300 import lagp as L
+    L.load()
+    return L
+
+
+def to_dev(a, dtype=None):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def gpu_run(L, w, search, precision, nrays=None, n_arr=None, nc_arr=None):
+    import torch
+    n = int(max(w.n, n_arr.max() if n_arr is not None else 0))
+    nc = int(max(w.nc, nc_arr.max() if nc_arr is not None else 0))
+    out = L.predict(to_dev(w.X), to_dev(w.Y), to_dev(w.Xref), w.n0, n, nc, w.theta, w.g,
+                    search=search, nrays=w.nrays if nrays is None else nrays,
+                    precision=precision,
+                    n_loc=to_dev(n_arr, torch.int32) if n_arr is not None else None,
+                    nclose_loc=to_dev(nc_arr, torch.int32) if nc_arr is not None else None,
+                    want_trace=True)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def oracle_run(w, search, nrays=None, n_arr=None, nc_arr=None):
+    n = int(max(w.n, n_arr.max() if n_arr is not None else 0))
+    nc = int(max(w.nc, nc_arr.max() if nc_arr is not None else 0))
+    return oracle.predict(w.X, w.Y, w.Xref, w.n0, n, nc, w.theta, w.g, search,
+                          nrays=w.nrays if nrays is None else nrays, n_arr=n_arr, nc_arr=nc_arr,
+                          nthreads=0)
+
+
+def assert_fp64_parity(g, o, n0, M, max_excused_frac=0.05):
+    """Returns (bit-identical locations, excused locations)."""
+    identical, excused = 0, 0
+    for m in range(M):
+        sg, so = g["selected"][m], o["selected"][m]
+        if np.array_equal(sg, so):
+            mo, mg = o["mean"][m], g["mean"][m]
+            assert abs(mg - mo) <= 1e-10 * max(abs(mo), 1e-300), (m, mg, mo)
+            assert abs(g["s2"][m] - o["s2"][m]) <= 1e-10 * abs(o["s2"][m]), m
+            if (mg == mo and g["s2"][m] == o["s2"][m]
+                    and np.array_equal(g["tie_gap"][m], o["gap"][m])):
+                identical += 1
+            continue
+        t = int(np.argmax(sg != so))
+        assert t >= n0, ("start (kNN) differs", m, t)
+        gap = o["gap"][m, t - n0]
+        assert gap < TIE_TOL, ("unexcused divergence", m, t, gap)
+        excused += 1
+    assert excused <= max_excused_frac * M
+    return identical, excused
+
+
+# --- kNN -------------------------------------------------------------------------
+
+def knn_gpu(L, X, Xref, nc):
+    import torch
+    N, p = X.shape
+    M = Xref.shape[0]
+    ws = torch.empty(L.laGP_knn_workspace_bytes(N, p, M, nc), dtype=torch.uint8, device="cuda")
+    cand = torch.empty((M, nc), dtype=torch.int32, device="cuda")
+    L.laGP_knn(to_dev(X), to_dev(Xref), nc, cand, ws)
+    rc, st = L.laGP_status(ws)
+    assert rc == 0, st
+    return cand.cpu().numpy()
+
+
+@pytest.mark.parametrize("p,N,M,nc", [(1, 3001, 37, 200), (3, 5000, 70, 300), (8, 9999, 33, 1000),
+                                      (13, 4097, 5, 700), (4, 257, 3, 257)])
+def test_knn_bit_exact(lagp, p, N, M, nc):
+    rng = np.random.default_rng(p * 7 + N)
+    X = rng.random((N, p))
+    Xref = rng.random((M, p)) * 1.2 - 0.1          # some outside the design's box
+    cand = knn_gpu(lagp, X, Xref, nc)
+    for m in range(M):
+        idx, _ = oracle.knn(X, Xref[m], nc)
+        np.testing.assert_array_equal(cand[m], idx)
+
+
+def test_knn_exact_ties_go_to_lower_index(lagp):
+    rng = np.random.default_rng(5)
+    X = rng.integers(0, 7, (6000, 3)).astype(np.float64)   # many duplicates and ties
+    Xref = rng.integers(0, 7, (20, 3)).astype(np.float64) + 0.5 * (rng.random((20, 3)) < 0.5)
+    cand = knn_gpu(lagp, X, Xref, 300)
+    for m in range(20):
+        idx, _ = oracle.knn(X, Xref[m], 300)
+        np.testing.assert_array_equal(cand[m], idx)
+
+
+# --- FP64 form ---------------------------------------------------------------------
+
+@pytest.mark.parametrize("search", ["exhaustive", "ray"])
+def test_fp64_dense_2d_full(lagp, search):
+    """The 2-d workload in full: N = 4000, M = 100, n = 30, N' = 500."""
+    w = W.dense_2d(M=100)
+    g = gpu_run(lagp, w, search, "fp64", nrays=2)
+    o = oracle_run(w, search, nrays=2)
+    ident, exc = assert_fp64_parity(g, o, w.n0, w.M)
+    assert ident >= 0.95 * w.M
+    if search == "ray":
+        np.testing.assert_array_equal(g["nevals"][:, : w.n - w.n0], o["nevals"][:, : w.n - w.n0])
+
+
+@pytest.mark.parametrize("case", [
+    dict(N=700, p=1, M=9, n0=3, n=12, nc=40, theta=0.01, g=1e-5, nrays=1),
+    dict(N=900, p=3, M=11, n0=5, n=5, nc=50, theta=0.1, g=1e-6, nrays=2),        # n = n0
+    dict(N=650, p=2, M=7, n0=4, n=20, nc=20, theta=0.05, g=1e-4, nrays=0),       # N' = n
+    dict(N=1300, p=5, M=13, n0=1, n=17, nc=300, theta=0.5, g=1e-8, nrays=5),     # n0 = 1
+    dict(N=2000, p=16, M=3, n0=6, n=40, nc=600, theta=4.0, g=1e-6, nrays=16),    # max p, rays
+])
+@pytest.mark.parametrize("search", ["exhaustive", "ray"])
+def test_fp64_edge_cases(lagp, case, search):
+    c = dict(case)
+    nr = c.pop("nrays")
+    if search == "ray" and (nr if nr > 0 else c["p"]) > c["nc"] - c["n"]:
+        pytest.skip("nrays > N' - n is outside the valid range")
+    w = W.small(seed=3, search=search, nrays=nr, **c)
+    g = gpu_run(lagp, w, search, "fp64")
+    o = oracle_run(w, search)
+    ident, _ = assert_fp64_parity(g, o, w.n0, w.M)
+    assert ident >= w.M - 1
+
+
+def test_fp64_max_local_design(lagp):
+    """n = 128 (the largest local design) with 16 rays and N' = 2000."""
+    w = W.small(N=6000, p=4, M=2, n0=6, n=128, nc=2000, theta=0.3, g=1e-6, seed=4,
+                search="ray", nrays=16)
+    g = gpu_run(lagp, w, "ray", "fp64")
+    o = oracle_run(w, "ray")
+    assert_fp64_parity(g, o, w.n0, w.M, max_excused_frac=0.5)
+
+
+def test_fp64_duplicate_design_ties(lagp):
+    w = W.small(N=400, p=2, M=6, n0=3, n=14, nc=60, theta=0.05, g=1e-4, seed=15)
+    w.X, w.Y = np.vstack([w.X, w.X]), np.concatenate([w.Y, w.Y])
+    w.N = 800
+    for search in ("exhaustive", "ray"):
+        g = gpu_run(lagp, w, search, "fp64", nrays=2)
+        o = oracle_run(w, search, nrays=2)
+        ident, _ = assert_fp64_parity(g, o, w.n0, w.M)
+        assert ident == w.M
+
+
+def test_fp64_uneven_sizes(lagp):
+    """Per-location n and N' in one launch."""
+    w = W.small(N=3000, p=3, M=24, n0=4, n=40, nc=400, theta=0.2, g=1e-6, seed=21)
+    rng = np.random.default_rng(1)
+    n_arr = rng.integers(6, 41, w.M).astype(np.int32)
+    nc_arr = rng.integers(60, 401, w.M).astype(np.int32)
+    for search in ("exhaustive", "ray"):
+        g = gpu_run(lagp, w, search, "fp64", nrays=3, n_arr=n_arr, nc_arr=nc_arr)
+        o = oracle_run(w, search, nrays=3, n_arr=n_arr, nc_arr=nc_arr)
+        for m in range(w.M):
+            assert np.all(g["selected"][m, n_arr[m]:] == -1)
+        ident, _ = assert_fp64_parity(g, o, w.n0, w.M)
+        assert ident >= w.M - 1
+
+
+def test_fp64_singular_update_reports_nan(lagp):
+    """g = 0 with duplicated nearest points: the Schur complement is 0; the
+    location gets NaN and the status word says so."""
+    import torch
+    X = np.array([[0.5, 0.5], [0.5, 0.5], [0.1, 0.9], [0.9, 0.1], [0.2, 0.2], [0.8, 0.8]] * 20)
+    X = X + np.repeat(np.arange(20)[:, None] * 1e-3, 6, axis=0)
+    Y = np.sin(X[:, 0])
+    Xref = np.array([[0.5, 0.5], [0.3, 0.7]])
+    o = oracle.predict(X, Y, Xref, 3, 8, 40, 0.1, 0.0, "exhaustive")
+    assert np.isnan(o["mean"][0]) and o["status"][0] != 0
+    L = lagp
+    ws = torch.empty(L.laGP_workspace_bytes(len(X), 2, 2, 8, 40, 0, 0, 0), dtype=torch.uint8,
+                     device="cuda")
+    mean = torch.empty(2, dtype=torch.float64, device="cuda")
+    s2 = torch.empty(2, dtype=torch.float64, device="cuda")
+    L.laGP_build_and_predict(to_dev(X), to_dev(Y), to_dev(Xref), 3, 8, 40, 0.1, 0.0, 0, 0, 0,
+                             mean, s2, ws)
+    rc, st = L.laGP_status(ws)
+    assert rc == -4 and st & 4
+    m = mean.cpu().numpy()
+    assert np.isnan(m[0]) and (np.isnan(o["mean"][1]) == np.isnan(m[1]))
+
+
+def test_host_buffer_entry_matches_device_entry(lagp):
+    import torch
+    L = lagp
+    w = W.small(N=2500, p=3, M=16, n0=4, n=20, nc=200, theta=0.2, g=1e-6, seed=8)
+    dev = gpu_run(L, w, "ray", "fp32", nrays=3)
+    wsb = L.laGP_host_workspace_bytes(w.N, w.p, w.M, w.n, w.nc, 3, 1, 1)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    mean, s2 = np.zeros(w.M), np.zeros(w.M)
+    sel = np.zeros((w.M, w.n), np.int32)
+    L.laGP_build_and_predict_host(w.X, w.Y, w.Xref, w.n0, w.n, w.nc, w.theta, w.g, 1, 3, 1,
+                                  mean, s2, ws, selected=sel)
+    np.testing.assert_array_equal(sel, dev["selected"])
+    np.testing.assert_array_equal(mean, dev["mean"])
+    np.testing.assert_array_equal(s2, dev["s2"])
+
+
+# --- 4-d paper-scale workload, sampled ---------------------------------------------
+
+@pytest.fixture(scope="module")
+def paper4d():
+    return W.paper_scale_4d(M=10000)
+
+
+def _sample(w, M):
+    s = W.Workload(**{k: getattr(w, k) for k in ("name", "N", "p", "M", "n0", "n", "nc",
+                                                 "theta", "g", "search", "nrays", "response")})
+    s.X, s.Y = w.X, w.Y
+    idx = np.linspace(0, w.M - 1, M).astype(int)
+    s.Xref, s.Ytrue, s.M = w.Xref[idx], w.Ytrue[idx], M
+    return s
+
+
+@pytest.mark.parametrize("search", ["exhaustive", "ray"])
+def test_fp64_paper_scale_4d_sample(lagp, paper4d, search):
+    w = _sample(paper4d, 48)
+    g = gpu_run(lagp, w, search, "fp64", nrays=4)
+    o = oracle_run(w, search, nrays=4)
+    ident, _ = assert_fp64_parity(g, o, w.n0, w.M)
+    assert ident >= 0.9 * w.M
+
+
+@pytest.mark.parametrize("search", ["exhaustive", "ray"])
+def test_fp32_score_paper_scale_4d_sample(lagp, paper4d, search):
+    w = _sample(paper4d, 200)
+    g = gpu_run(lagp, w, search, "fp32", nrays=4)
+    o = oracle_run(w, search, nrays=4)
+    same = np.all(g["selected"] == o["selected"], axis=1)
+    assert same.mean() > 0.5
+    rel = np.abs(g["s2"][same] - o["s2"][same]) / o["s2"][same]
+    assert np.all(rel <= 1e-4), rel.max()
+    rm_g = np.sqrt(np.mean((g["mean"] - w.Ytrue) ** 2))
+    rm_o = np.sqrt(np.mean((o["mean"] - w.Ytrue) ** 2))
+    assert rm_g <= 1.01 * rm_o, (rm_g, rm_o)
