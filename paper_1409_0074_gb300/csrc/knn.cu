@@ -377,9 +377,14 @@ size_t knn_smem_stream(int PP) {
   return (size_t)2 * LAGP_KNN_TILE * PP * 4 + 2 * LAGP_KNN_TILE * 4 + KNN_WARPS * 256 * 4 + 16;
 }
 
+// Buffer entries per location: room for N' survivors, a whole tile of new
+// inserts before the next compaction, and N'/2 (at least 64) entries of slack
+// for distances within the error margin of the N'-th.  A power of two, as the
+// bitonic sort of knn_rank wants.
 int knn_cap(int nc_max) {
+  const int need = nc_max + LAGP_KNN_TILE + (nc_max / 2 > 64 ? nc_max / 2 : 64);
   int cap = 512;
-  while (cap < 2 * nc_max) cap <<= 1;
+  while (cap < need) cap <<= 1;
   return cap;
 }
 
