@@ -132,6 +132,33 @@ int laGP_knn(const double* design, int64_t N, int p, const double* xref, int64_t
              int N_close, int32_t* cand, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * laGP_knn without a workspace: the same candidate search, with its scratch
+ * space in a fixed device array inside the library instead of caller memory.
+ * It serves callers that may not allocate device memory while they run (a
+ * host framework that owns all device memory through its own pool, a serving
+ * loop that cannot afford cudaMalloc's implicit device synchronisation, a
+ * deployment with a memory budget fixed at load time).  The paper has no
+ * counterpart; this is a deployment variant of step 1.
+ *
+ *   design, N, p, xref, M, N_close, cand: as in laGP_knn (device pointers)
+ *   status    device unsigned* or NULL: receives the LAGP_STATUS_* bits of
+ *             this call once the stream reaches the end of it
+ *   stream    cudaStream_t
+ * Limits: the scratch needed, laGP_knn_workspace_bytes(N, p, M, N_close),
+ * must not exceed LAGP_KNN_NOALLOC_SCRATCH_BYTES (64 MiB); larger requests
+ * return LAGP_ERR_WORKSPACE before any device work.  Every GPU that loads the
+ * library holds that array until the process exits.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All calls
+ * share the one array and each overwrites it: calls that overlap on the GPU
+ * (concurrent streams, threads or devices sharing a context) race, so
+ * serialise them.  No device memory is allocated or freed.
+ */
+#define LAGP_KNN_NOALLOC_SCRATCH_BYTES (64u << 20)
+int laGP_knn_noalloc(const double* design, int64_t N, int p, const double* xref, int64_t M,
+                     int N_close, int32_t* cand, unsigned* status, void* stream);
+
+/*
  * Waits for `stream`, then reads and clears the device status word of the
  * workspace.  *status receives the LAGP_STATUS_* bits.  Returns LAGP_OK when
  * no bit was set, LAGP_ERR_DEVICE when one was, LAGP_ERR_CUDA when the wait

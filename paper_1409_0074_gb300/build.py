@@ -23,6 +23,7 @@ UNITS = {
     "design_fp32.cu": [],
     "lagp_api.cu": [],
     "profile.cu": [],
+    "knn_noalloc.cu": [],
 }
 
 
