@@ -140,7 +140,7 @@ def kernel_flops(name, w, nevals_sum_j):
     the exhaustive FP32 scoring step j^2 + j + 4j per candidate."""
     if name == "knn_stream":
         return 3.0 * w["N"] * w["p"] * w["M_launch"]
-    if name == "design32_ray":
+    if name in ("design32_ray", "ray32"):
         s1, s2 = nevals_sum_j      # sum over evaluations of j and of j^2
         return s2 + (5 + 3 * w["p"] + 2) * s1
     return None

@@ -21,6 +21,7 @@ UNITS = {
     "knn.cu": [],
     "design_fp64.cu": ["--fmad=false"],
     "design_fp32.cu": [],
+    "ray32.cu": [],
     "lagp_api.cu": [],
     "profile.cu": [],
     "knn_noalloc.cu": [],

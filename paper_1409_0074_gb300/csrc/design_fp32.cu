@@ -1,5 +1,6 @@
-// design_fp32.cu -- greedy local design with FP32 candidate scoring and an
-// FP64 factor update, one CTA per predictive location.
+// design_fp32.cu -- exhaustive greedy local design with FP32 candidate scoring
+// and an FP64 factor update, one CTA per predictive location (the ray search
+// of this form is in ray32.cu).
 //
 // Scoring form.  With K_j = L_j L_j^T (Cholesky) the ALC integrand of Eq. alc
 // (sign reading as in the FP64 path) becomes
@@ -257,210 +258,6 @@ __device__ int search_exh32(const D32Params& P, L32& L, const int32_t* cl, int n
   return b.i;
 }
 
-// ----- ray search, FP32 evaluations (Sec 4) ---------------------------------------
-__device__ float warp_alc32(const D32Params& P, L32& L, const float* z) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int j = L.j, PP = P.PP, ldt = L.ldf;
-  float* kz = L.kzf + warp * P.n_max;
-  for (int i = lane; i < j; i += 32) {
-    const float* s = L.Sf + i * PP;
-    float d = 0.f;
-    for (int k = 0; k < PP; ++k) { float t = s[k] - z[k]; d = fmaf(t, t, d); }
-    kz[i] = __expf(d * L.neg_inv_theta);
-  }
-  __syncwarp();
-  float vs = 0.f, ns = 0.f;
-  for (int i = lane; i < j; i += 32) {
-    const float* Li = L.Lf + i * ldt;
-    float a0 = 0.f, a1 = 0.f;
-    int k = 0;
-    for (; k + 1 <= i; k += 2) { a0 = fmaf(Li[k], kz[k], a0); a1 = fmaf(Li[k + 1], kz[k + 1], a1); }
-    if (k <= i) a0 = fmaf(Li[k], kz[k], a0);
-    const float w = a0 + a1;
-    vs = fmaf(w, w, vs);
-    ns = fmaf(w, L.zf[i], ns);
-  }
-  vs = warp_sum(vs);
-  ns = warp_sum(ns);
-  float d = 0.f;
-  for (int k = 0; k < PP; ++k) { float t = z[k] - L.xf[k]; d = fmaf(t, t, d); }
-  __syncwarp();
-  const float v = L.onepg - vs;
-  const float num = ns - __expf(d * L.neg_inv_theta);
-  return v > 0.f ? num * num / v : 0.f;
-}
-
-__device__ float ray_f32(const D32Params& P, L32& L, const float* A, const float* E, float s) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float* z = L.rz + warp * P.PP;
-  if (lane < P.PP) z[lane] = fmaf(s, E[lane] - A[lane], A[lane]);
-  __syncwarp();
-  return -warp_alc32(P, L, z);
-}
-
-// Brent (1973) fmin on [0,1] in FP32 arithmetic, same constants as the FP64 path.
-__device__ float brent32(const D32Params& P, L32& L, const float* A, const float* E, float* xmin,
-                         int* nev) {
-  const float tol = 0x1p-13f, sqrt_eps = 0x1p-26f;
-  const float golden = 0.381966011250105151795f;
-  const float tol3 = tol / 3.f;
-  float a = 0.f, b = 1.f;
-  float x = a + golden * (b - a);
-  float w = x, v = x;
-  float fx = ray_f32(P, L, A, E, x);
-  float fw = fx, fv = fx, d = 0.f, e = 0.f;
-  int evals = 1;
-  for (int it = 0; it < 1000; ++it) {
-    const float m = 0.5f * (a + b);
-    const float tol1 = sqrt_eps * fabsf(x) + tol3;
-    const float tol2 = 2.f * tol1;
-    if (fabsf(x - m) <= tol2 - 0.5f * (b - a)) break;
-    bool golden_step = true;
-    if (fabsf(e) > tol1) {
-      float r = (x - w) * (fx - fv);
-      float q = (x - v) * (fx - fw);
-      float pn = (x - v) * q - (x - w) * r;
-      q = 2.f * (q - r);
-      if (q > 0.f) pn = -pn; else q = -q;
-      const float e_prev = e;
-      e = d;
-      if (fabsf(pn) < fabsf(0.5f * q * e_prev) && pn > q * (a - x) && pn < q * (b - x)) {
-        d = pn / q;
-        const float u_try = x + d;
-        if (u_try - a < tol2 || b - u_try < tol2) d = (m - x >= 0.f) ? tol1 : -tol1;
-        golden_step = false;
-      }
-    }
-    if (golden_step) {
-      e = (x < m) ? (b - x) : (a - x);
-      d = golden * e;
-    }
-    float u;
-    if (fabsf(d) >= tol1) u = x + d;
-    else if (d >= 0.f) u = x + tol1;
-    else u = x - tol1;
-    const float fu = ray_f32(P, L, A, E, u);
-    ++evals;
-    if (fu <= fx) {
-      if (u < x) b = x; else a = x;
-      v = w; fv = fw;
-      w = x; fw = fx;
-      x = u; fx = fu;
-    } else {
-      if (u < x) a = u; else b = u;
-      if (fu <= fw || w == x) {
-        v = w; fv = fw;
-        w = u; fw = fu;
-      } else if (fu <= fv || v == x || v == w) {
-        v = u; fv = fu;
-      }
-    }
-  }
-  *xmin = x;
-  *nev = evals;
-  return fx;
-}
-
-__device__ int search_ray32(const D32Params& P, L32& L, const int32_t* cl, int nc, double* gap_out,
-                            int* nev_out) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int PP = P.PP, R = P.R, j = L.j;
-  if (tid == 0) {
-    // starts: unselected candidates of rank k0, k0+1, ..., k0+R-1 (mod |U|)
-    const int nU = nc - j;
-    const int k0 = ray_offset(j, P.n0);
-    int seen = 0;
-    for (int r = 0; r < nc && seen < k0 + R; ++r) {
-      if (L.used[r]) continue;
-      const int t = seen - k0;
-      if (t >= 0) L.starts[t] = r;
-      ++seen;
-    }
-    for (int t = 0; t < R; ++t) {
-      if (k0 + t < nU) continue;
-      const int target = (k0 + t) % nU;
-      int s2 = 0, r = 0;
-      for (; r < nc; ++r) { if (L.used[r]) continue; if (s2 == target) break; ++s2; }
-      L.starts[t] = r < nc ? r : nc - 1;
-    }
-  }
-  __syncthreads();
-  for (int i = warp; i < R; i += D32_WARPS) {
-    float* A = L.rA + i * PP;
-    float* E = L.rE + i * PP;
-    if (lane < PP) A[lane] = cand_f(P, cl, L.starts[i])[lane];
-    __syncwarp();
-    if (lane == 0) {
-      float tau = 1.f;
-      for (int k = 0; k < P.p; ++k) {
-        const float dk = 10.f * (A[k] - L.xf[k]);
-        if (dk > 0.f) tau = fminf(tau, (L.hif[k] - A[k]) / dk);
-        else if (dk < 0.f) tau = fminf(tau, (L.lof[k] - A[k]) / dk);
-      }
-      tau = fmaxf(tau, 0.f);
-      for (int k = 0; k < PP; ++k) E[k] = fmaf(tau, 10.f * (A[k] - L.xf[k]), A[k]);
-    }
-    __syncwarp();
-    const float alc0 = warp_alc32(P, L, A);
-    int evals = 1;
-    float s_star = 0.f, alc_star = alc0;
-    float len2 = 0.f;
-    for (int k = 0; k < PP; ++k) { float t = E[k] - A[k]; len2 = fmaf(t, t, len2); }
-    if (len2 > 0.f) {
-      float sb;
-      int ne;
-      const float fb = brent32(P, L, A, E, &sb, &ne);
-      evals += ne;
-      if (!(alc0 >= -fb)) { s_star = sb; alc_star = -fb; }
-    }
-    if (lane == 0) { L.ralc[i] = alc_star; L.rs[i] = s_star; L.rnev[i] = evals; }
-    __syncwarp();
-  }
-  __syncthreads();
-  if (tid == 0) {
-    int ib = 0, ev = 0;
-    for (int i = 1; i < R; ++i) if (L.ralc[i] > L.ralc[ib]) ib = i;
-    float second = -1.f;
-    for (int i = 0; i < R; ++i) { ev += L.rnev[i]; if (i != ib) second = fmaxf(second, L.ralc[i]); }
-    const float* A = L.rA + ib * PP;
-    const float* E = L.rE + ib * PP;
-    for (int k = 0; k < PP; ++k) L.xs[k] = fmaf(L.rs[ib], E[k] - A[k], A[k]);
-    L.dscal[1] = (L.ralc[ib] > 0.f && R > 1) ? (double)((L.ralc[ib] - second) / L.ralc[ib]) : 0.0;
-    L.ired[0] = ev;
-  }
-  __syncthreads();
-  // snap (FP32 distances; ties to the lower rank)
-  for (int pass = 0; pass < 2; ++pass) {
-    VI t; t.v = -__int_as_float(0x7f800000); t.v2 = t.v; t.i = -1;
-    for (int r = tid; r < nc; r += blockDim.x) {
-      if (L.used[r]) continue;
-      const float* c = cand_f(P, cl, r);
-      if (pass == 0) {
-        bool forbidden = false;
-        for (int i = 0; i < R; ++i) {
-          if (L.starts[i] != r) continue;
-          bool same = true;
-          for (int k = 0; k < PP; ++k) if (c[k] != L.xs[k]) same = false;
-          if (!same) forbidden = true;
-        }
-        if (forbidden) continue;
-      }
-      float d = 0.f;
-      for (int k = 0; k < PP; ++k) { float q = c[k] - L.xs[k]; d = fmaf(q, q, d); }
-      const float nd = -d;   // maximise -d
-      if (nd > t.v) { t.v2 = t.v; t.v = nd; t.i = r; }
-      else if (nd > t.v2) t.v2 = nd;
-    }
-    VI b = block_best(t, L.red, L.ired + 1);
-    if (b.i >= 0 || pass == 1) {
-      *gap_out = L.dscal[1];
-      *nev_out = L.ired[0];
-      return b.i;
-    }
-  }
-  return -1;
-}
-
 template <int SEARCH>
 __global__ void __launch_bounds__(D32_THREADS) design32(D32Params P) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -528,8 +325,7 @@ __global__ void __launch_bounds__(D32_THREADS) design32(D32Params P) {
   for (int j = P.n0; j < n && ok; ++j) {
     double gap = 0.0;
     int ne = 0;
-    int r = (SEARCH == 0) ? search_exh32(P, L, cl, nc, Kc_loc, &gap)
-                          : search_ray32(P, L, cl, nc, &gap, &ne);
+    int r = search_exh32(P, L, cl, nc, Kc_loc, &gap);
     if (tid == 0) {
       if (P.tie_gap) P.tie_gap[loc * ld + (j - P.n0)] = gap;
       if (P.nevals) P.nevals[loc * ld + (j - P.n0)] = ne;
@@ -570,6 +366,7 @@ static size_t smem_design32(int n_max, int p, int PP, int nc_max, int R, int sea
 }
 
 cudaError_t launch_design_fp32(const DesignArgs& a, int search, cudaStream_t s) {
+  if (search != 0) return launch_ray32(a, s);
   D32Params P;
   P.X = a.X; P.Y = a.Y; P.p = a.p; P.PP = a.PP; P.Xf = a.ws->Xf; P.xref = a.xref; P.M = a.M;
   P.cand = a.cand; P.nc_max = a.nc_max; P.nc_loc = a.nc_loc; P.n0 = a.n0; P.n_max = a.n_max;
@@ -577,21 +374,13 @@ cudaError_t launch_design_fp32(const DesignArgs& a, int search, cudaStream_t s) 
   P.hi = a.ws->hi; P.center = a.ws->center; P.mean = a.mean; P.s2 = a.s2;
   P.selected = a.selected; P.tie_gap = a.tie_gap; P.nevals = a.nevals; P.Linv = a.ws->state64;
   P.Kc = a.ws->state32; P.status = a.ws->status;
-  size_t sm = smem_design32(a.n_max, a.p, a.PP, a.nc_max, a.nrays, search);
-  cudaError_t err;
-  if (search == 0) {
-    err = cudaFuncSetAttribute(design32<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (err != cudaSuccess) return err;
-    prof_begin("design32_exhaustive", s);
-    design32<0><<<(unsigned)a.M, D32_THREADS, sm, s>>>(P);
-    prof_end(s);
-  } else {
-    err = cudaFuncSetAttribute(design32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (err != cudaSuccess) return err;
-    prof_begin("design32_ray", s);
-    design32<1><<<(unsigned)a.M, D32_THREADS, sm, s>>>(P);
-    prof_end(s);
-  }
+  size_t sm = smem_design32(a.n_max, a.p, a.PP, a.nc_max, a.nrays, 0);
+  cudaError_t err =
+      cudaFuncSetAttribute(design32<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (err != cudaSuccess) return err;
+  prof_begin("design32_exhaustive", s);
+  design32<0><<<(unsigned)a.M, D32_THREADS, sm, s>>>(P);
+  prof_end(s);
   return cudaGetLastError();
 }
 

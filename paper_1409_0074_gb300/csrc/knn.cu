@@ -316,7 +316,9 @@ knn_stream(const float* __restrict__ Xf, const float* __restrict__ nx, int64_t N
 
 // ---------------------------------------------------------------------------
 // Exact ranking: binary64 distances in the oracle's order, bitonic sort of
-// (d64, index), first N' indices out.
+// (d64, index), first N' indices out.  Distances are non-negative, so their
+// IEEE bit patterns order like the values: the sort compares 64-bit integers
+// (FP64 compares would run on GB300's narrow FP64 pipe).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
 knn_rank(const double* __restrict__ X, int p, const double* __restrict__ xref, int64_t M,
@@ -328,7 +330,7 @@ knn_rank(const double* __restrict__ X, int p, const double* __restrict__ xref, i
   if (q >= M) return;
   const int c = cnt[q];
   const int nc = nc_loc ? nc_loc[q] : nc_max;
-  double* key = reinterpret_cast<double*>(smem_rank);
+  unsigned long long* key = reinterpret_cast<unsigned long long*>(smem_rank);
   int32_t* idx = reinterpret_cast<int32_t*>(key + cap);
   __shared__ double xq[LAGP_MAX_P];
   if (threadIdx.x < p) xq[threadIdx.x] = xref[q * p + threadIdx.x];
@@ -339,27 +341,27 @@ knn_rank(const double* __restrict__ X, int p, const double* __restrict__ xref, i
   for (int i = threadIdx.x; i < sz; i += blockDim.x) {
     if (i < c) {
       int32_t gi = e[i].idx;
-      key[i] = sqdist64(X + (int64_t)gi * p, xq, p);
+      key[i] = (unsigned long long)__double_as_longlong(sqdist64(X + (int64_t)gi * p, xq, p));
       idx[i] = gi;
     } else {
-      key[i] = __longlong_as_double(0x7ff0000000000000ll);
+      key[i] = ~0ull;
       idx[i] = 0x7fffffff;
     }
   }
   __syncthreads();
   for (int k = 2; k <= sz; k <<= 1) {
     for (int jj = k >> 1; jj > 0; jj >>= 1) {
-      for (int i = threadIdx.x; i < sz; i += blockDim.x) {
-        int l = i ^ jj;
-        if (l > i) {
-          bool up = (i & k) == 0;
-          double ki = key[i], kl = key[l];
-          int32_t ii = idx[i], il = idx[l];
-          bool gt = (ki > kl) || (ki == kl && ii > il);
-          if (gt == up) {
-            key[i] = kl; key[l] = ki;
-            idx[i] = il; idx[l] = ii;
-          }
+      for (int t = threadIdx.x; t < (sz >> 1); t += blockDim.x) {
+        // t-th compare-exchange pair of this stage
+        const int i = ((t & ~(jj - 1)) << 1) | (t & (jj - 1));
+        const int l = i | jj;
+        const bool up = (i & k) == 0;
+        const unsigned long long ki = key[i], kl = key[l];
+        const int32_t ii = idx[i], il = idx[l];
+        const bool gt = (ki > kl) || (ki == kl && ii > il);
+        if (gt == up) {
+          key[i] = kl; key[l] = ki;
+          idx[i] = il; idx[l] = ii;
         }
       }
       __syncthreads();

@@ -43,7 +43,10 @@ size_t layout_workspace(const Shape& sh, void* base, Workspace* ws) {
   if (sh.precision == LAGP_FP64) {
     if (sh.search == LAGP_EXHAUSTIVE) s64 = sizeof(double) * c * sh.n_max * sh.nc_max;
   } else {
-    s64 = sizeof(double) * c * sh.n_max * sh.n_max;
+    const size_t per = (size_t)sh.n_max * sh.n_max > ray32_g64_doubles(sh.n_max)
+                           ? (size_t)sh.n_max * sh.n_max
+                           : ray32_g64_doubles(sh.n_max);
+    s64 = sizeof(double) * c * per;
     if (sh.search == LAGP_EXHAUSTIVE) s32 = sizeof(float) * c * sh.n_max * sh.nc_max;
   }
   w.state64 = static_cast<double*>(take(s64));

@@ -80,6 +80,10 @@ void prof_begin(const char* name, cudaStream_t s);
 void prof_end(cudaStream_t s);
 
 cudaError_t launch_design_fp64(const DesignArgs& a, int search, cudaStream_t s);
+// FP32-scoring ray search, one warp per location (ray32.cu); its per-location
+// FP64 scratch in Workspace::state64 holds ray32_g64_doubles(n_max) doubles.
+cudaError_t launch_ray32(const DesignArgs& a, cudaStream_t s);
+size_t ray32_g64_doubles(int n_max);
 cudaError_t launch_design_fp32(const DesignArgs& a, int search, cudaStream_t s);
 
 }  // namespace lagp

@@ -1,0 +1,514 @@
+// ray32.cu -- ray search (Gramacy & Haaland, Sec 4) with FP32 scoring and an
+// FP64 factor update, one warp per predictive location.
+//
+// Lane layout.  With R rays padded to RP (a power of two) and G = 32 / RP,
+// lane = r * G + q works for ray r on every G-th row (q, q+G, ...) of each
+// ALC evaluation.  All rays of a location advance together: a round evaluates
+// ALC once for every ray still searching (its s = 0 point, its first golden-
+// section point, or its next Brent trial point), then each ray updates its
+// own Brent (1973) state.  A ray that has converged idles until the last ray
+// of its location is done.  The warp never meets a CTA-wide barrier.
+//
+// Scoring (FP32, through the inverse Cholesky factor, as in design_fp32.cu):
+//   kz_k = exp(-|S_k - z|^2 / theta),  w = L^{-1} kz,
+//   ALC(z) = (w . (L^{-1} k(x)) - K(z, x))^2 / (1 + g - |w|^2).
+// L^{-1} (FP32) sits in shared memory as lower-triangular rows padded with
+// zeros to a multiple of 4, so every row is read as float4s.
+// The factor itself grows in FP64 (the partitioned update in factored form,
+// Sec 2.2) in global memory, packed lower-triangular.
+#include <cstdint>
+
+#include "common.cuh"
+#include "lagp_internal.h"
+
+namespace lagp {
+
+#define RW_WARPS 2                  // locations per CTA
+#define RAY_MAX_ROUNDS 1100         // bound on evaluation rounds per step
+
+struct RayParams {
+  const double* X;
+  const double* Y;
+  int p, PP;
+  const float* Xf;
+  const double* xref;
+  int64_t M;
+  const int32_t* cand;
+  int nc_max;
+  const int32_t* nc_loc;
+  int n0, n_max;
+  const int32_t* n_loc;
+  double theta, g;
+  int R;
+  const double* lo;
+  const double* hi;
+  const double* center;
+  double* mean;
+  double* s2;
+  int32_t* selected;
+  double* tie_gap;
+  int32_t* nevals;
+  double* g64;          // per location: packed L^{-1} (n(n+1)/2) then kx, z, zy, kvec, l (n each)
+  int64_t g64_stride;
+  unsigned* status;
+};
+
+// start of row i in the zero-padded FP32 row storage (rows of length
+// (i+1) rounded up to a multiple of 4)
+__device__ __host__ __forceinline__ int roff(int i) {
+  const int a = i >> 2, b = i & 3;
+  return 4 * (i + 2 * a * (a - 1) + a * b);
+}
+__device__ __host__ __forceinline__ int tri(int i) { return i * (i + 1) / 2; }
+// row length of the kz buffer: a multiple of 4 whose quarter is odd, so that
+// the rays' float4 reads fall on different banks
+__device__ __host__ __forceinline__ int kz_ld(int n) {
+  int k = (n + 3) & ~3;
+  if (((k >> 2) & 1) == 0) k += 4;
+  return k;
+}
+
+struct WarpLayout {
+  int lf, kz, zf, sf, ae, x, sel, starts, mask, bytes;
+};
+
+__host__ __device__ inline WarpLayout warp_layout(int n, int PP, int RP, int nc) {
+  WarpLayout w;
+  int off = 0;   // in 4-byte words, float region first (16-byte aligned pieces)
+  auto take = [&](int words) { int o = off; off += (words + 3) & ~3; return o; };
+  w.lf = take(roff(n));
+  w.kz = take(RP * kz_ld(n));
+  w.zf = take((n + 3) & ~3);
+  w.sf = take(n * PP);
+  w.ae = take(2 * RP * PP);
+  w.x = take(4 * PP);          // xf, lof, hif, xs
+  w.sel = take(n);
+  w.starts = take(RP);
+  w.mask = take((nc + 31) / 32);
+  w.bytes = off * 4;
+  return w;
+}
+
+struct Brent {
+  float a, b, x, w, v, fx, fw, fv, d, e;
+};
+
+// Brent (1973) fmin on [0,1]: from the current state, either report
+// convergence (false) or produce the next trial point u (true).  Same
+// constants as the FP64 path: tol = 2^-13, sqrt(eps) = 2^-26.
+__device__ __forceinline__ bool brent_next(Brent& s, float* u_out) {
+  const float tol3 = 0x1p-13f / 3.f, sqrt_eps = 0x1p-26f;
+  const float golden = 0.381966011250105151795f;
+  const float m = 0.5f * (s.a + s.b);
+  const float tol1 = sqrt_eps * fabsf(s.x) + tol3;
+  const float tol2 = 2.f * tol1;
+  if (fabsf(s.x - m) <= tol2 - 0.5f * (s.b - s.a)) return false;
+  bool golden_step = true;
+  if (fabsf(s.e) > tol1) {
+    float r = (s.x - s.w) * (s.fx - s.fv);
+    float q = (s.x - s.v) * (s.fx - s.fw);
+    float pn = (s.x - s.v) * q - (s.x - s.w) * r;
+    q = 2.f * (q - r);
+    if (q > 0.f) pn = -pn; else q = -q;
+    const float e_prev = s.e;
+    s.e = s.d;
+    if (fabsf(pn) < fabsf(0.5f * q * e_prev) && pn > q * (s.a - s.x) && pn < q * (s.b - s.x)) {
+      s.d = pn / q;
+      const float u_try = s.x + s.d;
+      if (u_try - s.a < tol2 || s.b - u_try < tol2) s.d = (m - s.x >= 0.f) ? tol1 : -tol1;
+      golden_step = false;
+    }
+  }
+  if (golden_step) {
+    s.e = (s.x < m) ? (s.b - s.x) : (s.a - s.x);
+    s.d = golden * s.e;
+  }
+  float u;
+  if (fabsf(s.d) >= tol1) u = s.x + s.d;
+  else if (s.d >= 0.f) u = s.x + tol1;
+  else u = s.x - tol1;
+  *u_out = u;
+  return true;
+}
+
+__device__ __forceinline__ void brent_take(Brent& s, float u, float fu) {
+  if (fu <= s.fx) {
+    if (u < s.x) s.b = s.x; else s.a = s.x;
+    s.v = s.w; s.fv = s.fw;
+    s.w = s.x; s.fw = s.fx;
+    s.x = u; s.fx = fu;
+  } else {
+    if (u < s.x) s.a = u; else s.b = u;
+    if (fu <= s.fw || s.w == s.x) {
+      s.v = s.w; s.fv = s.fw;
+      s.w = u; s.fw = fu;
+    } else if (fu <= s.fv || s.v == s.x || s.v == s.w) {
+      s.v = u; s.fv = fu;
+    }
+  }
+}
+
+__device__ __forceinline__ double warp_sum64(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+enum { PH_ALC0 = 0, PH_FIRST = 1, PH_ITER = 2, PH_DONE = 3 };
+
+template <int RP, int PP>
+__global__ void __launch_bounds__(RW_WARPS * 32) ray32_kernel(RayParams P) {
+  extern __shared__ __align__(16) float sm[];
+  constexpr int G = 32 / RP;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t loc = (int64_t)blockIdx.x * RW_WARPS + warp;
+  if (loc >= P.M) return;
+
+  const int p = P.p, ldn = P.n_max, R = P.R;
+  const int nc = P.nc_loc ? P.nc_loc[loc] : P.nc_max;
+  const int n = P.n_loc ? P.n_loc[loc] : P.n_max;
+  const int32_t* cl = P.cand + loc * P.nc_max;
+  const WarpLayout lay = warp_layout(ldn, PP, RP, P.nc_max);
+  float* base = sm + (size_t)warp * (lay.bytes / 4);
+  float* Lf = base + lay.lf;
+  float* kzb = base + lay.kz;
+  float* zf = base + lay.zf;
+  float* Sf = base + lay.sf;
+  float* Ab = base + lay.ae;
+  float* Eb = Ab + RP * PP;
+  float* xf = base + lay.x;
+  float* lof = xf + PP;
+  float* hif = lof + PP;
+  float* xs = hif + PP;
+  int* sel = reinterpret_cast<int*>(base + lay.sel);
+  int* starts = reinterpret_cast<int*>(base + lay.starts);
+  uint32_t* mask = reinterpret_cast<uint32_t*>(base + lay.mask);
+  const int KP = kz_ld(ldn);
+
+  double* Lg = P.g64 + loc * P.g64_stride;
+  double* kx64 = Lg + tri(ldn);
+  double* z64 = kx64 + ldn;
+  double* zy64 = z64 + ldn;
+  double* kv64 = zy64 + ldn;
+  double* l64 = kv64 + ldn;
+  const double* xq = P.xref + loc * p;
+
+  const float nit = (float)(-1.0 / P.theta);
+  const float onepg = (float)(1.0 + P.g);
+
+  for (int i = lane; i < roff(ldn); i += 32) Lf[i] = 0.f;
+  for (int i = lane; i < RP * KP; i += 32) kzb[i] = 0.f;
+  for (int i = lane; i < (P.nc_max + 31) / 32; i += 32) mask[i] = 0u;
+  if (lane < PP) {
+    const bool in = lane < p;
+    xf[lane] = in ? (float)(xq[lane] - P.center[lane]) : 0.f;
+    lof[lane] = in ? (float)(P.lo[lane] - P.center[lane]) : 0.f;
+    hif[lane] = in ? (float)(P.hi[lane] - P.center[lane]) : 0.f;
+  }
+  if (P.tie_gap) for (int i = lane; i < ldn; i += 32) P.tie_gap[loc * ldn + i] = 0.0;
+  if (P.nevals) for (int i = lane; i < ldn; i += 32) P.nevals[loc * ldn + i] = 0;
+  __syncwarp();
+
+  int j = 0;
+  bool ok = (n >= P.n0) && (n <= nc) && (n <= ldn);
+
+  // ---- append candidate rank rr to the design (FP64 factor row) ----
+  auto add_point = [&](int rr) -> bool {
+    const double* c64 = P.X + (int64_t)cl[rr] * p;
+    for (int i = lane; i < j; i += 32) kv64[i] = corr64(P.X + (int64_t)cl[sel[i]] * p, c64, p, P.theta);
+    __syncwarp();
+    double vv = 0.0;
+    for (int i = lane; i < j; i += 32) {
+      const double* Li = Lg + tri(i);
+      double acc = 0.0;
+      for (int k = 0; k <= i; ++k) acc = fma(Li[k], kv64[k], acc);
+      l64[i] = acc;
+      vv = fma(acc, acc, vv);
+    }
+    vv = warp_sum64(vv);
+    __syncwarp();
+    const double v = (1.0 + P.g) - vv;
+    if (!(v > 0.0)) return false;
+    const double inv_d = 1.0 / sqrt(v);
+    double* Lj = Lg + tri(j);
+    float* Lfj = Lf + roff(j);
+    for (int k = lane; k < j; k += 32) {
+      double acc = 0.0;
+      for (int i = k; i < j; ++i) acc = fma(l64[i], Lg[tri(i) + k], acc);
+      const double rk = -acc * inv_d;
+      Lj[k] = rk;
+      Lfj[k] = (float)rk;
+    }
+    if (lane == 0) {
+      Lj[j] = inv_d;
+      Lfj[j] = (float)inv_d;
+      kx64[j] = corr64(c64, xq, p, P.theta);
+      sel[j] = rr;
+      mask[rr >> 5] |= 1u << (rr & 31);
+    }
+    if (lane < PP) Sf[j * PP + lane] = P.Xf[(int64_t)cl[rr] * PP + lane];
+    __syncwarp();
+    double zz = 0.0, zyy = 0.0;
+    for (int k = lane; k <= j; k += 32) {
+      const double rk = Lj[k];
+      zz = fma(rk, kx64[k], zz);
+      zyy = fma(rk, P.Y[cl[sel[k]]], zyy);
+    }
+    zz = warp_sum64(zz);
+    zyy = warp_sum64(zyy);
+    if (lane == 0) {
+      z64[j] = zz;
+      zy64[j] = zyy;
+      zf[j] = (float)zz;
+    }
+    __syncwarp();
+    ++j;
+    return true;
+  };
+
+  for (int rr = 0; rr < P.n0 && ok; ++rr) ok = add_point(rr);
+
+  const int r = lane / G, q = lane % G;
+  for (int step = P.n0; step < n && ok; ++step) {
+    // ---- ray starts: unselected candidates of rank k0, k0+1, ... (mod |U|) ----
+    if (lane == 0) {
+      const int nU = nc - j;
+      const int k0 = ray_offset(j, P.n0);
+      for (int t = 0; t < R; ++t) {
+        const int target = (k0 + t) % nU;
+        int seen = 0, rr = nc - 1;
+        for (int wd = 0; wd * 32 < nc; ++wd) {
+          const int hi = min(32, nc - wd * 32);
+          uint32_t un = ~mask[wd] & (hi == 32 ? 0xffffffffu : ((1u << hi) - 1u));
+          const int c = __popc(un);
+          if (seen + c <= target) { seen += c; continue; }
+          for (int b = target - seen; b > 0; --b) un &= un - 1u;   // drop lower bits
+          rr = wd * 32 + __ffs(un) - 1;
+          break;
+        }
+        starts[t] = rr;
+      }
+    }
+    __syncwarp();
+    // ---- segments (FP32): end = A + tau * 10 (A - x), cut at the design's box ----
+    const bool ray_live = r < R;
+    float len2 = 0.f;
+    if (ray_live) {
+      const float* a = P.Xf + (int64_t)cl[starts[r]] * PP;
+      float tau = 1.f;
+      for (int k = 0; k < p; ++k) {
+        const float dk = 10.f * (a[k] - xf[k]);
+        if (dk > 0.f) tau = fminf(tau, (hif[k] - a[k]) / dk);
+        else if (dk < 0.f) tau = fminf(tau, (lof[k] - a[k]) / dk);
+      }
+      tau = fmaxf(tau, 0.f);
+      for (int k = 0; k < PP; ++k) {
+        const float ak = a[k];
+        const float ek = fmaf(tau, 10.f * (ak - xf[k]), ak);
+        if (q == 0) { Ab[r * PP + k] = ak; Eb[r * PP + k] = ek; }
+        len2 = fmaf(ek - ak, ek - ak, len2);
+      }
+    }
+    __syncwarp();
+
+    // ---- lockstep Brent over the rays ----
+    int phase = ray_live ? PH_ALC0 : PH_DONE;
+    float s_eval = 0.f, alc0 = 0.f, s_star = 0.f, alc_star = 0.f;
+    int evals = 0;
+    Brent st;
+    st.a = 0.f; st.b = 1.f; st.x = st.w = st.v = 0.f; st.fx = st.fw = st.fv = 0.f;
+    st.d = 0.f; st.e = 0.f;
+    for (int round = 0; round < RAY_MAX_ROUNDS; ++round) {
+      const bool active = phase != PH_DONE;
+      if (!__any_sync(0xffffffffu, active)) break;
+      float zc[PP];
+#pragma unroll
+      for (int c = 0; c < PP; ++c) zc[c] = 0.f;
+      float* kzr = kzb + r * KP;
+      if (active) {
+#pragma unroll
+        for (int c = 0; c < PP; ++c) {
+          const float ac = Ab[r * PP + c];
+          zc[c] = fmaf(s_eval, Eb[r * PP + c] - ac, ac);
+        }
+        for (int k = q; k < j; k += G) {
+          const float* sk = Sf + k * PP;
+          float d = 0.f;
+#pragma unroll
+          for (int c = 0; c < PP; c += 4) {
+            const float4 s4 = *reinterpret_cast<const float4*>(sk + c);
+            float t0 = s4.x - zc[c], t1 = s4.y - zc[c + 1], t2 = s4.z - zc[c + 2],
+                  t3 = s4.w - zc[c + 3];
+            d = fmaf(t0, t0, d); d = fmaf(t1, t1, d); d = fmaf(t2, t2, d); d = fmaf(t3, t3, d);
+          }
+          kzr[k] = __expf(d * nit);
+        }
+      }
+      __syncwarp();
+      float vs = 0.f, ns = 0.f;
+      if (active) {
+        for (int i = q; i < j; i += G) {
+          const float* Li = Lf + roff(i);
+          const int len = (i + 4) & ~3;
+          float w0 = 0.f, w1 = 0.f;
+          for (int k = 0; k < len; k += 4) {
+            const float4 l4 = *reinterpret_cast<const float4*>(Li + k);
+            const float4 k4 = *reinterpret_cast<const float4*>(kzr + k);
+            w0 = fmaf(l4.x, k4.x, w0); w1 = fmaf(l4.y, k4.y, w1);
+            w0 = fmaf(l4.z, k4.z, w0); w1 = fmaf(l4.w, k4.w, w1);
+          }
+          const float w = w0 + w1;
+          vs = fmaf(w, w, vs);
+          ns = fmaf(w, zf[i], ns);
+        }
+      }
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) {
+        vs += __shfl_xor_sync(0xffffffffu, vs, o);
+        ns += __shfl_xor_sync(0xffffffffu, ns, o);
+      }
+      float val = 0.f;
+      if (active) {
+        float d = 0.f;
+#pragma unroll
+        for (int c = 0; c < PP; ++c) { const float t = zc[c] - xf[c]; d = fmaf(t, t, d); }
+        const float v = onepg - vs;
+        const float num = ns - __expf(d * nit);
+        val = v > 0.f ? num * num / v : 0.f;
+      }
+      __syncwarp();
+      if (active) {
+        ++evals;
+        bool more = false;
+        float u = 0.f;
+        if (phase == PH_ALC0) {
+          alc0 = val;
+          if (len2 > 0.f) { phase = PH_FIRST; s_eval = 0.381966011250105151795f; more = true; }
+        } else if (phase == PH_FIRST) {
+          st.x = st.w = st.v = s_eval;
+          st.fx = st.fw = st.fv = -val;
+          more = brent_next(st, &u);
+          if (more) { s_eval = u; phase = PH_ITER; }
+        } else {
+          brent_take(st, s_eval, -val);
+          more = brent_next(st, &u);
+          if (more) s_eval = u;
+        }
+        if (more && evals > 1000) more = false;
+        if (!more) {
+          if (phase == PH_ALC0 || alc0 >= -st.fx) { s_star = 0.f; alc_star = alc0; }
+          else { s_star = st.x; alc_star = -st.fx; }
+          phase = PH_DONE;
+        }
+      }
+    }
+    // ---- best ray, its continuous point x* ----
+    float best = -1.f, second = -1.f;
+    int ib = 0, ev = 0;
+    for (int rr = 0; rr < R; ++rr) {
+      const float a_r = __shfl_sync(0xffffffffu, alc_star, rr * G);
+      ev += __shfl_sync(0xffffffffu, evals, rr * G);
+      if (a_r > best) { second = best; best = a_r; ib = rr; }
+      else if (a_r > second) second = a_r;
+    }
+    const float sb = __shfl_sync(0xffffffffu, s_star, ib * G);
+    if (lane < PP) xs[lane] = fmaf(sb, Eb[ib * PP + lane] - Ab[ib * PP + lane], Ab[ib * PP + lane]);
+    __syncwarp();
+    // ---- snap: nearest allowed unselected candidate (ties to the lower rank) ----
+    int pick = -1;
+    for (int pass = 0; pass < 2 && pick < 0; ++pass) {
+      float bd = __int_as_float(0x7f800000);
+      int bi = 0x7fffffff;
+      for (int rr = lane; rr < nc; rr += 32) {
+        if (mask[rr >> 5] & (1u << (rr & 31))) continue;
+        const float* c = P.Xf + (int64_t)cl[rr] * PP;
+        bool same = true;
+        float d = 0.f;
+        for (int k = 0; k < PP; ++k) {
+          const float t = c[k] - xs[k];
+          same = same && (t == 0.f);
+          d = fmaf(t, t, d);
+        }
+        if (pass == 0 && !same) {
+          bool is_start = false;
+          for (int t = 0; t < R; ++t) is_start |= (starts[t] == rr);
+          if (is_start) continue;
+        }
+        if (d < bd) { bd = d; bi = rr; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const float od = __shfl_xor_sync(0xffffffffu, bd, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (od < bd || (od == bd && oi < bi)) { bd = od; bi = oi; }
+      }
+      if (bi != 0x7fffffff) pick = bi;
+    }
+    if (lane == 0) {
+      if (P.tie_gap) P.tie_gap[loc * ldn + (step - P.n0)] =
+          (best > 0.f && R > 1) ? (double)((best - second) / best) : 0.0;
+      if (P.nevals) P.nevals[loc * ldn + (step - P.n0)] = ev;
+    }
+    ok = (pick >= 0) && add_point(pick);
+  }
+
+  if (ok) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int i = lane; i < j; i += 32) {
+      a = fma(z64[i], zy64[i], a);
+      b = fma(zy64[i], zy64[i], b);
+      c = fma(z64[i], z64[i], c);
+    }
+    a = warp_sum64(a);
+    b = warp_sum64(b);
+    c = warp_sum64(c);
+    if (lane == 0) {
+      P.mean[loc] = a;
+      P.s2[loc] = b * ((1.0 + P.g) - c) / (double)j;
+    }
+  } else if (lane == 0) {
+    P.mean[loc] = __longlong_as_double(0x7ff8000000000000ll);
+    P.s2[loc] = __longlong_as_double(0x7ff8000000000000ll);
+    atomicOr(P.status, LAGP_DEV_BAD_UPDATE);
+  }
+  if (P.selected)
+    for (int i = lane; i < ldn; i += 32) P.selected[loc * ldn + i] = (i < j) ? cl[sel[i]] : -1;
+}
+
+size_t ray32_g64_doubles(int n_max) { return (size_t)tri(n_max) + 5 * (size_t)n_max; }
+
+cudaError_t launch_ray32(const DesignArgs& a, cudaStream_t s) {
+  RayParams P;
+  P.X = a.X; P.Y = a.Y; P.p = a.p; P.PP = a.PP; P.Xf = a.ws->Xf; P.xref = a.xref; P.M = a.M;
+  P.cand = a.cand; P.nc_max = a.nc_max; P.nc_loc = a.nc_loc; P.n0 = a.n0; P.n_max = a.n_max;
+  P.n_loc = a.n_loc; P.theta = a.theta; P.g = a.g; P.R = a.nrays; P.lo = a.ws->lo;
+  P.hi = a.ws->hi; P.center = a.ws->center; P.mean = a.mean; P.s2 = a.s2;
+  P.selected = a.selected; P.tie_gap = a.tie_gap; P.nevals = a.nevals; P.g64 = a.ws->state64;
+  P.g64_stride = (int64_t)ray32_g64_doubles(a.n_max); P.status = a.ws->status;
+  int RP = 2;
+  while (RP < a.nrays) RP <<= 1;
+  const WarpLayout lay = warp_layout(a.n_max, a.PP, RP, a.nc_max);
+  const size_t sm = (size_t)lay.bytes * RW_WARPS;
+  const unsigned grid = (unsigned)((a.M + RW_WARPS - 1) / RW_WARPS);
+  cudaError_t err = cudaSuccess;
+  const int key = RP * 100 + a.PP;
+  switch (key) {
+#define RAY_CASE(RPV, PPV)                                                                   \
+  case RPV * 100 + PPV:                                                                      \
+    err = cudaFuncSetAttribute(ray32_kernel<RPV, PPV>,                                       \
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);        \
+    if (err != cudaSuccess) return err;                                                      \
+    prof_begin("ray32", s);                                                                  \
+    ray32_kernel<RPV, PPV><<<grid, RW_WARPS * 32, sm, s>>>(P);                               \
+    prof_end(s);                                                                             \
+    break;
+    RAY_CASE(2, 4) RAY_CASE(2, 8) RAY_CASE(2, 12) RAY_CASE(2, 16)
+    RAY_CASE(4, 4) RAY_CASE(4, 8) RAY_CASE(4, 12) RAY_CASE(4, 16)
+    RAY_CASE(8, 4) RAY_CASE(8, 8) RAY_CASE(8, 12) RAY_CASE(8, 16)
+    RAY_CASE(16, 4) RAY_CASE(16, 8) RAY_CASE(16, 12) RAY_CASE(16, 16)
+#undef RAY_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace lagp
