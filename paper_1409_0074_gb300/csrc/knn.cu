@@ -80,7 +80,8 @@ __global__ void bbox_final(const double* __restrict__ part, int nparts, int p,
 }
 
 // Xf[i][0..PP) = fl32(X[i] - center) (zero padded), nx[i] = |Xf[i]|^2 in FP32;
-// rows N..Npad-1 are zero.  maxn2 receives max_i nx[i] (as ordered bits).
+// rows N..Npad-1 are zero with nx = 1e30.  maxn2 receives max_{i<N} nx[i]
+// (as ordered bits).
 __global__ void design_to_f32(const double* __restrict__ X, int64_t N, int64_t Npad, int p, int PP,
                               const double* __restrict__ center, float* __restrict__ Xf,
                               float* __restrict__ nx, unsigned* __restrict__ maxn2_bits) {
@@ -94,8 +95,9 @@ __global__ void design_to_f32(const double* __restrict__ X, int64_t N, int64_t N
       Xf[i * PP + k] = v;
       acc = fmaf(v, v, acc);
     }
-    nx[i] = acc;
-    local_max = fmaxf(local_max, acc);
+    // padding rows get |x|^2 = 1e30, so that no distance to them passes
+    nx[i] = i < N ? acc : 1e30f;
+    if (i < N) local_max = fmaxf(local_max, acc);
   }
   for (int o = 16; o > 0; o >>= 1) local_max = fmaxf(local_max, __shfl_xor_sync(0xffffffffu, local_max, o));
   if ((threadIdx.x & 31) == 0) atomicMax(maxn2_bits, __float_as_uint(local_max));
@@ -171,7 +173,7 @@ __device__ int warp_compact(KnnEntry* e, int cnt, float keep) {
 }
 
 template <int PP>
-__global__ void __launch_bounds__(KNN_WARPS * 32)
+__global__ void __launch_bounds__(KNN_WARPS * 32, 3)
 knn_stream(const float* __restrict__ Xf, const float* __restrict__ nx, int64_t N, int64_t ntiles,
            int p, const double* __restrict__ xref, int64_t M, const double* __restrict__ center,
            const unsigned* __restrict__ maxn2_bits, int nc_max, const int32_t* __restrict__ nc_loc,
@@ -186,7 +188,6 @@ knn_stream(const float* __restrict__ Xf, const float* __restrict__ nx, int64_t N
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t q0 = (int64_t)blockIdx.x * (KNN_WARPS * KNN_QW) + warp * KNN_QW;
 
-  // per-location state (warp-uniform)
   float qf[KNN_QW][PP], nq[KNN_QW], err[KNN_QW], keep[KNN_QW];
   int cnt[KNN_QW], ncq[KNN_QW];
   bool live[KNN_QW];
@@ -205,9 +206,8 @@ knn_stream(const float* __restrict__ Xf, const float* __restrict__ nx, int64_t N
     }
     nq[a] = acc;
     float r = rmax + sqrtf(acc) * 1.0001f;
-    // |d32 - d64| <= (p + 12) 2^-24 (|a| + |b|)^2, with a 25% margin
     err[a] = (float)(p + 12) * 0x1p-24f * 1.25f * r * r;
-    keep[a] = __int_as_float(0x7f800000);
+    keep[a] = live[a] ? __int_as_float(0x7f800000) : -1.f;
     cnt[a] = 0;
     ncq[a] = live[a] ? (nc_loc ? nc_loc[q] : nc_max) : 0;
   }
@@ -258,19 +258,22 @@ knn_stream(const float* __restrict__ Xf, const float* __restrict__ nx, int64_t N
         xv[k] = v4.x; xv[k + 1] = v4.y; xv[k + 2] = v4.z; xv[k + 3] = v4.w;
       }
       const float nxp = TN[pt];
-      const bool valid = gi < N;
+      float d[KNN_QW];
 #pragma unroll
       for (int a = 0; a < KNN_QW; ++a) {
         float dot = 0.f;
 #pragma unroll
         for (int k = 0; k < PP; ++k) dot = fmaf(qf[a][k], xv[k], dot);
-        float d = fmaxf(fmaf(-2.f, dot, nq[a] + nxp), 0.f);
-        bool pass = live[a] && valid && d <= keep[a];
+        d[a] = fmaf(-2.f, dot, nq[a] + nxp);
+      }
+#pragma unroll
+      for (int a = 0; a < KNN_QW; ++a) {
+        const bool pass = d[a] <= keep[a];
         uint32_t m = __ballot_sync(0xffffffffu, pass);
         if (m) {
           int pos = cnt[a] + __popc(m & ((1u << lane) - 1u));
           if (pass && pos < cap) {
-            KnnEntry e; e.d = d; e.idx = (int32_t)gi;
+            KnnEntry e; e.d = fmaxf(d[a], 0.f); e.idx = (int32_t)gi;
             buf[(q0 + a) * (int64_t)cap + pos] = e;
           }
           cnt[a] += __popc(m);

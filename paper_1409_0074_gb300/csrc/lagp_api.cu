@@ -10,9 +10,14 @@ namespace lagp {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static int64_t chunk_for(int64_t M, int search, int precision) {
-  int64_t cap = 65536;
+// Locations per chunk: bounded by a per-search cap and by keeping the kNN
+// candidate buffers within 16 GiB.
+static int64_t chunk_for(int64_t M, int search, int precision, int nc_max, int64_t N) {
+  int64_t cap = 131072;
   if (search == LAGP_EXHAUSTIVE) cap = (precision == LAGP_FP64) ? 16384 : 32768;
+  const int64_t per_loc = (int64_t)8 * knn_cap(nc_max);
+  const int64_t by_mem = ((int64_t)16 << 30) / per_loc;
+  if (by_mem < cap) cap = by_mem > 128 ? by_mem : 128;
   return M < cap ? (M > 0 ? M : 1) : cap;
 }
 
@@ -77,7 +82,7 @@ static bool make_shape(int64_t N, int p, int64_t M, int n0, int n, int N_close, 
   sh->nrays = (search == LAGP_RAY) ? R : 1;
   sh->search = search;
   sh->precision = precision;
-  sh->chunk = chunk_for(M, search, precision);
+  sh->chunk = chunk_for(M, search, precision, N_close, N);
   return true;
 }
 
