@@ -22,6 +22,7 @@ UNITS = {
     "design_fp64.cu": ["--fmad=false"],
     "design_fp32.cu": [],
     "ray32.cu": [],
+    "exh_tc.cu": [],
     "lagp_api.cu": [],
     "profile.cu": [],
     "knn_noalloc.cu": [],

@@ -367,6 +367,7 @@ static size_t smem_design32(int n_max, int p, int PP, int nc_max, int R, int sea
 
 cudaError_t launch_design_fp32(const DesignArgs& a, int search, cudaStream_t s) {
   if (search != 0) return launch_ray32(a, s);
+  if (exh_tc_supported(a.n_max)) return launch_exh_tc(a, s);
   D32Params P;
   P.X = a.X; P.Y = a.Y; P.p = a.p; P.PP = a.PP; P.Xf = a.ws->Xf; P.xref = a.xref; P.M = a.M;
   P.cand = a.cand; P.nc_max = a.nc_max; P.nc_loc = a.nc_loc; P.n0 = a.n0; P.n_max = a.n_max;

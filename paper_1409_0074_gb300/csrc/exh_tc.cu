@@ -1,0 +1,407 @@
+// exh_tc.cu -- exhaustive greedy local design (Gramacy & Haaland, Sec 2.2) with
+// the candidate scores of every step computed as a dense contraction on the
+// tensor cores, one CTA (4 warps) per predictive location; local designs up to
+// n = 64.
+//
+// Scoring (the factored form of Eq. alc, as in design_fp32.cu): with the
+// correlation rows Kc (N' x j, Kc[r][i] = K(c_r, S_i)) and the inverse
+// Cholesky factor L_j^{-1},
+//     W = Kc L_j^{-T}   (row r: w_r = L_j^{-1} k_j(c_r)),
+//     v_r = 1 + g - |w_r|^2,  num_r = w_r . z - K(c_r, x),  ALC_r = num_r^2 / v_r,
+// z = L_j^{-1} k_j(x).  W is a tcgen05.mma kind::tf32 product of 128-candidate
+// tiles (M = 128) with L_j^{-1} (N = j rounded up to 16, K = j rounded up to
+// 8), 3xTF32 (hi*hi + hi*lo + lo*hi, FP32 accumulation in TMEM).  Thread t of
+// the CTA owns candidate row t of a tile: it writes that row of the A operand,
+// reads its row of W back from TMEM (tcgen05.ld 32x32b) and reduces v and
+// num.  The block argmax (ties to the lower rank) picks the next point.
+//
+// FP64 state (the partitioned update in factored form, Sec 2.2): L_j^{-1} in
+// global memory, grown by one row per step, and z, L^{-1} y; the predictive
+// equations (Eq. predgp, preds2) at the end.  Each new row of L^{-1} is also
+// written, split into TF32 hi + lo, into the B operand in shared memory; the
+// correlation cache gains one row (N' exponentials) per step.
+#include <cstdint>
+
+#include "common.cuh"
+#include "lagp_internal.h"
+
+namespace lagp {
+
+#define XT_THREADS 128
+#define XT_KMAX 64     // largest local design on this path
+
+struct XtParams {
+  const double* X;
+  const double* Y;
+  int p, PP;
+  const float* Xf;
+  const double* xref;
+  int64_t M;
+  const int32_t* cand;
+  int nc_max;
+  const int32_t* nc_loc;
+  int n0, n_max;
+  const int32_t* n_loc;
+  double theta, g;
+  const double* center;
+  double* mean;
+  double* s2;
+  int32_t* selected;
+  double* tie_gap;
+  int32_t* nevals;
+  double* Linv;          // [M][n_max][n_max]
+  float* Kc;             // [M][n_max][nc_max]
+  unsigned* status;
+};
+
+// canonical no-swizzle K-major layout with XT_KMAX columns per row
+__device__ __forceinline__ uint32_t xcanon(int row, int k) {
+  return (uint32_t)((row >> 3) * ((XT_KMAX >> 2) * 128) + (k >> 2) * 128 + (row & 7) * 16 +
+                    (k & 3) * 4);
+}
+
+__device__ __forceinline__ float xtf32(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ uint64_t xdesc(uint32_t addr) {
+  const uint32_t lbo = 128, sbo = (XT_KMAX / 4) * 128;
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void xmma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                     uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// 16 columns of this thread's TMEM lane
+__device__ __forceinline__ void xld16(uint32_t addr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ double xsum(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < XT_THREADS / 32; ++w) t += red[w];
+  return t;
+}
+
+struct XtSmem {
+  static constexpr int B_BYTES = XT_KMAX * XT_KMAX * 4;   // L^{-1} rows, one of hi / lo
+  static constexpr int A_BYTES = 128 * XT_KMAX * 4;       // candidate tile, one of hi / lo
+  static constexpr int B_OFF = 0;
+  static constexpr int A_OFF = 2 * B_BYTES;
+  static constexpr int END = A_OFF + 2 * A_BYTES;         // 96 KB
+};
+
+__global__ void __launch_bounds__(XT_THREADS) exh_tc_kernel(XtParams P) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  float* Bhi = reinterpret_cast<float*>(smem + XtSmem::B_OFF);
+  float* Blo = Bhi + XtSmem::B_BYTES / 4;
+  float* Ahi = reinterpret_cast<float*>(smem + XtSmem::A_OFF);
+  float* Alo = Ahi + XtSmem::A_BYTES / 4;
+  const int p = P.p, PP = P.PP, ld = P.n_max, nc_max = P.nc_max;
+  // small state after the operands
+  float* kap = reinterpret_cast<float*>(smem + XtSmem::END);          // [nc_max]
+  float* zf = kap + ((nc_max + 3) & ~3);                             // [XT_KMAX]
+  double* S64 = reinterpret_cast<double*>(zf + XT_KMAX);              // [XT_KMAX][p], 16B aligned
+  double* kx = S64 + XT_KMAX * p;                                     // [XT_KMAX]
+  double* z = kx + XT_KMAX;
+  double* zy = z + XT_KMAX;
+  double* kv = zy + XT_KMAX;
+  double* lv = kv + XT_KMAX;
+  double* red = lv + XT_KMAX;                                         // [8]
+  float* fred = reinterpret_cast<float*>(red + 8);                    // [8]
+  int* ired = reinterpret_cast<int*>(fred + 8);                       // [8]
+  int* sel = ired + 8;                                                // [XT_KMAX]
+  unsigned char* used = reinterpret_cast<unsigned char*>(sel + XT_KMAX);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(
+      (reinterpret_cast<uintptr_t>(used + nc_max) + 15) & ~(uintptr_t)15);
+  uint32_t* tbase = reinterpret_cast<uint32_t*>(bar + 1);
+
+  const int64_t loc = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nc = P.nc_loc ? P.nc_loc[loc] : nc_max;
+  const int n = P.n_loc ? P.n_loc[loc] : P.n_max;
+  const int32_t* cl = P.cand + loc * nc_max;
+  double* Lg = P.Linv + loc * (int64_t)ld * ld;
+  float* Kc = P.Kc + loc * (int64_t)ld * nc_max;
+  const double* xq = P.xref + loc * p;
+  const float nit = (float)(-1.0 / P.theta);
+  const float onepg = (float)(1.0 + P.g);
+
+  for (int i = tid; i < 2 * XtSmem::B_BYTES / 4; i += XT_THREADS) Bhi[i] = 0.f;
+  for (int r = tid; r < nc; r += XT_THREADS) {
+    used[r] = 0;
+    const float* c = P.Xf + (int64_t)cl[r] * PP;
+    float d = 0.f;
+    for (int k = 0; k < p; ++k) {
+      const float t = c[k] - (float)(xq[k] - P.center[k]);
+      d = fmaf(t, t, d);
+    }
+    kap[r] = __expf(d * nit);
+  }
+  if (P.tie_gap) for (int i = tid; i < ld; i += XT_THREADS) P.tie_gap[loc * ld + i] = 0.0;
+  if (P.nevals) for (int i = tid; i < ld; i += XT_THREADS) P.nevals[loc * ld + i] = 0;
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(
+        smem_u32(tbase)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t taddr = *tbase;
+
+  int j = 0;
+  uint32_t phase = 0;
+  bool ok = (n >= P.n0) && (n <= nc) && (n <= ld) && (ld <= XT_KMAX);
+
+  // ---- append candidate rank rr: FP64 factor row, z, L^{-1}y, B row, Kc row ----
+  auto add_point = [&](int rr) -> bool {
+    const double* c = P.X + (int64_t)cl[rr] * p;
+    if (tid < p) S64[j * p + tid] = c[tid];
+    __syncthreads();
+    for (int i = tid; i < j; i += XT_THREADS) kv[i] = corr64(S64 + i * p, S64 + j * p, p, P.theta);
+    __syncthreads();
+    double vv = 0.0;
+    for (int i = tid; i < j; i += XT_THREADS) {
+      const double* Li = Lg + (int64_t)i * ld;
+      double acc = 0.0;
+      for (int k = 0; k <= i; ++k) acc = fma(Li[k], kv[k], acc);
+      lv[i] = acc;
+      vv = fma(acc, acc, vv);
+    }
+    vv = xsum(vv, red);
+    const double v = (1.0 + P.g) - vv;
+    if (!(v > 0.0)) return false;
+    const double inv_d = 1.0 / sqrt(v);
+    for (int k = tid; k <= j; k += XT_THREADS) {
+      double rk = inv_d;
+      if (k < j) {
+        double acc = 0.0;
+        for (int i = k; i < j; ++i) acc = fma(lv[i], Lg[(int64_t)i * ld + k], acc);
+        rk = -acc * inv_d;
+      }
+      Lg[(int64_t)j * ld + k] = rk;
+      const float h = xtf32((float)rk);
+      const uint32_t off = xcanon(j, k) >> 2;
+      Bhi[off] = h;
+      Blo[off] = xtf32((float)(rk - (double)h));
+    }
+    if (tid == 0) {
+      kx[j] = corr64(S64 + j * p, xq, p, P.theta);
+      sel[j] = rr;
+      used[rr] = 1;
+    }
+    __syncthreads();
+    double zz = 0.0, zyy = 0.0;
+    for (int k = tid; k <= j; k += XT_THREADS) {
+      const double rk = Lg[(int64_t)j * ld + k];
+      zz = fma(rk, kx[k], zz);
+      zyy = fma(rk, P.Y[cl[sel[k]]], zyy);
+    }
+    zz = xsum(zz, red);
+    zyy = xsum(zyy, red);
+    if (tid == 0) {
+      z[j] = zz;
+      zy[j] = zyy;
+      zf[j] = (float)zz;
+    }
+    // correlation cache row j: K(c_r, S_j) for every candidate
+    const float* sj = P.Xf + (int64_t)cl[rr] * PP;
+    for (int q = tid; q < nc; q += XT_THREADS) {
+      const float* cq = P.Xf + (int64_t)cl[q] * PP;
+      float d = 0.f;
+      for (int k = 0; k < PP; ++k) { const float t = cq[k] - sj[k]; d = fmaf(t, t, d); }
+      Kc[(int64_t)j * nc_max + q] = __expf(d * nit);
+    }
+    __syncthreads();
+    ++j;
+    return true;
+  };
+
+  for (int rr = 0; rr < P.n0 && ok; ++rr) ok = add_point(rr);
+
+  for (int step = P.n0; step < n && ok; ++step) {
+    const int jn = (j + 15) & ~15;       // N of the MMA
+    const int jk = (j + 7) & ~7;         // K of the MMA
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(jn >> 3) << 17) |
+                           ((uint32_t)(128 >> 4) << 24);
+    float best = -1.f, second = -1.f;
+    int bi = -1;
+    for (int base = 0; base < nc; base += 128) {
+      // A operand: this thread's candidate row, hi / lo, zero past j
+      const int r = base + tid;
+      const bool live = r < nc;
+#pragma unroll 4
+      for (int k = 0; k < jk; k += 4) {
+        float4 h, l;
+        float vals[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          vals[u] = (live && k + u < j) ? Kc[(int64_t)(k + u) * nc_max + r] : 0.f;
+        h.x = xtf32(vals[0]); h.y = xtf32(vals[1]); h.z = xtf32(vals[2]); h.w = xtf32(vals[3]);
+        l.x = xtf32(vals[0] - h.x); l.y = xtf32(vals[1] - h.y);
+        l.z = xtf32(vals[2] - h.z); l.w = xtf32(vals[3] - h.w);
+        const uint32_t off = xcanon(tid, k) >> 2;
+        *reinterpret_cast<float4*>(Ahi + off) = h;
+        *reinterpret_cast<float4*>(Alo + off) = l;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo);
+        const uint32_t bh = smem_u32(Bhi), bl = smem_u32(Blo);
+        for (int ks = 0; ks < jk / 8; ++ks) {
+          const uint32_t ko = ks * 256;
+          xmma(taddr, xdesc(ah + ko), xdesc(bh + ko), idesc, ks > 0 ? 1u : 0u);
+          xmma(taddr, xdesc(ah + ko), xdesc(bl + ko), idesc, 1u);
+          xmma(taddr, xdesc(al + ko), xdesc(bh + ko), idesc, 1u);
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(bar))
+                     : "memory");
+      }
+      bool done = mbar_wait(bar, phase);
+      phase ^= 1u;
+      if (!__syncthreads_and(done)) {
+        if (tid == 0) atomicOr(P.status, LAGP_DEV_TIMEOUT);
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // epilogue: row tid of W
+      float vs = 0.f, ns = 0.f;
+      const uint32_t row = taddr + ((uint32_t)(warp * 32) << 16);
+      for (int c0 = 0; c0 < jn; c0 += 16) {
+        float w[16];
+        xld16(row + c0, w);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int i = c0 + u;
+          const float wi = i < j ? w[u] : 0.f;
+          vs = fmaf(wi, wi, vs);
+          ns = fmaf(wi, i < j ? zf[i] : 0.f, ns);
+        }
+      }
+      if (live && !used[r]) {
+        const float v = onepg - vs;
+        const float num = ns - kap[r];
+        const float alc = v > 0.f ? num * num / v : 0.f;
+        if (alc > best) { second = best; best = alc; bi = r; }
+        else if (alc > second) second = alc;
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+    }
+    if (!ok) break;
+    // block argmax, ties to the lower rank; the second best for the gap
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const float os = __shfl_xor_sync(0xffffffffu, second, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi >= 0 && (bi < 0 || oi < bi))) {
+        second = fmaxf(best, os); best = ob; bi = oi;
+      } else {
+        second = fmaxf(second, ob);
+      }
+    }
+    if (lane == 0) { fred[2 * warp] = best; fred[2 * warp + 1] = second; ired[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      float b = fred[0], s = fred[1];
+      int ii = ired[0];
+      for (int w = 1; w < XT_THREADS / 32; ++w) {
+        const float ob = fred[2 * w], os = fred[2 * w + 1];
+        const int oi = ired[w];
+        if (ob > b || (ob == b && oi >= 0 && (ii < 0 || oi < ii))) { s = fmaxf(b, os); b = ob; ii = oi; }
+        else s = fmaxf(s, ob);
+      }
+      ired[4] = ii;
+      if (P.tie_gap) P.tie_gap[loc * ld + (step - P.n0)] = (b > 0.f && s >= 0.f) ? (double)((b - s) / b) : 0.0;
+    }
+    __syncthreads();
+    const int pick = ired[4];
+    ok = (pick >= 0) && add_point(pick);
+  }
+
+  if (ok) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int i = tid; i < j; i += XT_THREADS) {
+      a = fma(z[i], zy[i], a);
+      b = fma(zy[i], zy[i], b);
+      c = fma(z[i], z[i], c);
+    }
+    a = xsum(a, red);
+    b = xsum(b, red);
+    c = xsum(c, red);
+    if (tid == 0) {
+      P.mean[loc] = a;
+      P.s2[loc] = b * ((1.0 + P.g) - c) / (double)j;
+    }
+  } else if (tid == 0) {
+    P.mean[loc] = __longlong_as_double(0x7ff8000000000000ll);
+    P.s2[loc] = __longlong_as_double(0x7ff8000000000000ll);
+    atomicOr(P.status, LAGP_DEV_BAD_UPDATE);
+  }
+  if (P.selected)
+    for (int i = tid; i < ld; i += XT_THREADS) P.selected[loc * ld + i] = (i < j) ? cl[sel[i]] : -1;
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(taddr));
+  }
+}
+
+bool exh_tc_supported(int n_max) { return n_max <= XT_KMAX; }
+
+cudaError_t launch_exh_tc(const DesignArgs& a, cudaStream_t s) {
+  XtParams P;
+  P.X = a.X; P.Y = a.Y; P.p = a.p; P.PP = a.PP; P.Xf = a.ws->Xf; P.xref = a.xref; P.M = a.M;
+  P.cand = a.cand; P.nc_max = a.nc_max; P.nc_loc = a.nc_loc; P.n0 = a.n0; P.n_max = a.n_max;
+  P.n_loc = a.n_loc; P.theta = a.theta; P.g = a.g; P.center = a.ws->center; P.mean = a.mean;
+  P.s2 = a.s2; P.selected = a.selected; P.tie_gap = a.tie_gap; P.nevals = a.nevals;
+  P.Linv = a.ws->state64; P.Kc = a.ws->state32; P.status = a.ws->status;
+  const size_t small = (size_t)((a.nc_max + 3) & ~3) * 4 + XT_KMAX * 4 + (size_t)XT_KMAX * a.p * 8 +
+                       5 * XT_KMAX * 8 + 8 * 8 + 8 * 4 + 8 * 4 + XT_KMAX * 4 + a.nc_max + 64;
+  const size_t sm = 1024 + XtSmem::END + small;
+  cudaError_t err =
+      cudaFuncSetAttribute(exh_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (err != cudaSuccess) return err;
+  prof_begin("exh_tc", s);
+  exh_tc_kernel<<<(unsigned)a.M, XT_THREADS, sm, s>>>(P);
+  prof_end(s);
+  return cudaGetLastError();
+}
+
+}  // namespace lagp

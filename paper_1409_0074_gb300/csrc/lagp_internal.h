@@ -83,6 +83,9 @@ cudaError_t launch_design_fp64(const DesignArgs& a, int search, cudaStream_t s);
 // FP32-scoring ray search, one warp per location (ray32.cu); its per-location
 // FP64 scratch in Workspace::state64 holds ray32_g64_doubles(n_max) doubles.
 cudaError_t launch_ray32(const DesignArgs& a, cudaStream_t s);
+// FP32-scoring exhaustive search with tensor-core scoring (exh_tc.cu), n_max <= 64.
+bool exh_tc_supported(int n_max);
+cudaError_t launch_exh_tc(const DesignArgs& a, cudaStream_t s);
 size_t ray32_g64_doubles(int n_max);
 cudaError_t launch_design_fp32(const DesignArgs& a, int search, cudaStream_t s);
 
