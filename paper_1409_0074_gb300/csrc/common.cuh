@@ -60,6 +60,21 @@ __device__ __forceinline__ double sqdist64(const double* a, const double* b, int
   return acc;
 }
 
+// Squared distance in binary32 between a row of the FP32 design copy (global,
+// 16-byte aligned, PP a multiple of 4: read as float4) and any PP floats, in
+// ascending coordinate order with one FMA per coordinate.
+__device__ __forceinline__ float sqdist_row32(const float* __restrict__ row, const float* b, int PP) {
+  float d = 0.f;
+  for (int k = 0; k < PP; k += 4) {
+    const float4 c = *reinterpret_cast<const float4*>(row + k);
+    float t = c.x - b[k]; d = fmaf(t, t, d);
+    t = c.y - b[k + 1]; d = fmaf(t, t, d);
+    t = c.z - b[k + 2]; d = fmaf(t, t, d);
+    t = c.w - b[k + 3]; d = fmaf(t, t, d);
+  }
+  return d;
+}
+
 // Isotropic Gaussian correlation exp(-||a-b||^2 / theta) in binary64.
 __device__ __forceinline__ double corr64(const double* a, const double* b, int p, double theta) {
   return exp_cw(-(__ddiv_rn(sqdist64(a, b, p), theta)));

@@ -201,12 +201,8 @@ __device__ bool add_point32(const D32Params& P, L32& L, const int32_t* cl, int n
   if (SEARCH == 0) {
     float* row = Kc_loc + (int64_t)j * P.nc_max;
     const float* sj = L.Sf + j * P.PP;
-    for (int q = tid; q < nc; q += blockDim.x) {
-      const float* cq = cand_f(P, cl, q);
-      float d = 0.f;
-      for (int k = 0; k < P.PP; ++k) { float t = cq[k] - sj[k]; d = fmaf(t, t, d); }
-      row[q] = __expf(d * L.neg_inv_theta);
-    }
+    for (int q = tid; q < nc; q += blockDim.x)
+      row[q] = __expf(sqdist_row32(cand_f(P, cl, q), sj, P.PP) * L.neg_inv_theta);
   }
   __syncthreads();
   L.j = j + 1;
@@ -242,9 +238,7 @@ __device__ int search_exh32(const D32Params& P, L32& L, const int32_t* cl, int n
         vs = fmaf(w, w, vs);
         ns = fmaf(w, L.zf[i], ns);
       }
-      const float* cr = cand_f(P, cl, r);
-      float d = 0.f;
-      for (int k = 0; k < P.PP; ++k) { float t = cr[k] - L.xf[k]; d = fmaf(t, t, d); }
+      const float d = sqdist_row32(cand_f(P, cl, r), L.xf, P.PP);
       const float v = L.onepg - vs;
       const float num = ns - __expf(d * L.neg_inv_theta);
       const float alc = v > 0.f ? num * num / v : 0.f;

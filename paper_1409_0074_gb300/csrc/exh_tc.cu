@@ -237,12 +237,8 @@ __global__ void __launch_bounds__(XT_THREADS) exh_tc_kernel(XtParams P) {
     }
     // correlation cache row j: K(c_r, S_j) for every candidate
     const float* sj = P.Xf + (int64_t)cl[rr] * PP;
-    for (int q = tid; q < nc; q += XT_THREADS) {
-      const float* cq = P.Xf + (int64_t)cl[q] * PP;
-      float d = 0.f;
-      for (int k = 0; k < PP; ++k) { const float t = cq[k] - sj[k]; d = fmaf(t, t, d); }
-      Kc[(int64_t)j * nc_max + q] = __expf(d * nit);
-    }
+    for (int q = tid; q < nc; q += XT_THREADS)
+      Kc[(int64_t)j * nc_max + q] = __expf(sqdist_row32(P.Xf + (int64_t)cl[q] * PP, sj, PP) * nit);
     __syncthreads();
     ++j;
     return true;

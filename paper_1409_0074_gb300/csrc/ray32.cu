@@ -69,7 +69,7 @@ __device__ __host__ __forceinline__ int kz_ld(int n) {
 }
 
 struct WarpLayout {
-  int lf, kz, zf, sf, ae, x, sel, starts, mask, bytes;
+  int lf, kz, zf, sf, ae, x, sel, starts, mask, smask, bytes;
 };
 
 __host__ __device__ inline WarpLayout warp_layout(int n, int PP, int RP, int nc) {
@@ -85,6 +85,7 @@ __host__ __device__ inline WarpLayout warp_layout(int n, int PP, int RP, int nc)
   w.sel = take(n);
   w.starts = take(RP);
   w.mask = take((nc + 31) / 32);
+  w.smask = take((nc + 31) / 32);
   w.bytes = off * 4;
   return w;
 }
@@ -181,7 +182,8 @@ __global__ void __launch_bounds__(RW_WARPS * 32) ray32_kernel(RayParams P) {
   float* xs = hif + PP;
   int* sel = reinterpret_cast<int*>(base + lay.sel);
   int* starts = reinterpret_cast<int*>(base + lay.starts);
-  uint32_t* mask = reinterpret_cast<uint32_t*>(base + lay.mask);
+  uint32_t* mask = reinterpret_cast<uint32_t*>(base + lay.mask);     // selected candidates
+  uint32_t* smask = reinterpret_cast<uint32_t*>(base + lay.smask);   // this step's ray starts
   const int KP = kz_ld(ldn);
 
   double* Lg = P.g64 + loc * P.g64_stride;
@@ -197,7 +199,7 @@ __global__ void __launch_bounds__(RW_WARPS * 32) ray32_kernel(RayParams P) {
 
   for (int i = lane; i < roff(ldn); i += 32) Lf[i] = 0.f;
   for (int i = lane; i < RP * KP; i += 32) kzb[i] = 0.f;
-  for (int i = lane; i < (P.nc_max + 31) / 32; i += 32) mask[i] = 0u;
+  for (int i = lane; i < (P.nc_max + 31) / 32; i += 32) { mask[i] = 0u; smask[i] = 0u; }
   if (lane < PP) {
     const bool in = lane < p;
     xf[lane] = in ? (float)(xq[lane] - P.center[lane]) : 0.f;
@@ -270,22 +272,39 @@ __global__ void __launch_bounds__(RW_WARPS * 32) ray32_kernel(RayParams P) {
   const int r = lane / G, q = lane % G;
   for (int step = P.n0; step < n && ok; ++step) {
     // ---- ray starts: unselected candidates of rank k0, k0+1, ... (mod |U|) ----
-    if (lane == 0) {
+    // lane l owns mask words l, l + 32, ...; a warp scan of their unselected
+    // counts locates the word holding each target rank
+    {
       const int nU = nc - j;
       const int k0 = ray_offset(j, P.n0);
-      for (int t = 0; t < R; ++t) {
-        const int target = (k0 + t) % nU;
-        int seen = 0, rr = nc - 1;
-        for (int wd = 0; wd * 32 < nc; ++wd) {
+      const int nw = (nc + 31) >> 5;
+      int seen = 0;
+      for (int w0 = 0; w0 < nw; w0 += 32) {
+        const int wd = w0 + lane;
+        uint32_t un = 0u;
+        if (wd < nw) {
           const int hi = min(32, nc - wd * 32);
-          uint32_t un = ~mask[wd] & (hi == 32 ? 0xffffffffu : ((1u << hi) - 1u));
-          const int c = __popc(un);
-          if (seen + c <= target) { seen += c; continue; }
-          for (int b = target - seen; b > 0; --b) un &= un - 1u;   // drop lower bits
-          rr = wd * 32 + __ffs(un) - 1;
-          break;
+          un = ~mask[wd] & (hi == 32 ? 0xffffffffu : ((1u << hi) - 1u));
         }
-        starts[t] = rr;
+        const int c = __popc(un);
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const int first = seen + incl - c;
+        for (int t = 0; t < R; ++t) {
+          const int target = (k0 + t) % nU;
+          if (target >= first && target < first + c) {
+            uint32_t u = un;
+            for (int q2 = target - first; q2 > 0; --q2) u &= u - 1u;   // drop lower bits
+            const int rr = wd * 32 + __ffs(u) - 1;
+            starts[t] = rr;
+            smask[wd] |= 1u << (rr & 31);   // words are lane-owned: no race
+          }
+        }
+        seen += __shfl_sync(0xffffffffu, incl, 31);
       }
     }
     __syncwarp();
@@ -414,34 +433,48 @@ __global__ void __launch_bounds__(RW_WARPS * 32) ray32_kernel(RayParams P) {
     if (lane < PP) xs[lane] = fmaf(sb, Eb[ib * PP + lane] - Ab[ib * PP + lane], Ab[ib * PP + lane]);
     __syncwarp();
     // ---- snap: nearest allowed unselected candidate (ties to the lower rank) ----
-    int pick = -1;
-    for (int pass = 0; pass < 2 && pick < 0; ++pass) {
-      float bd = __int_as_float(0x7f800000);
-      int bi = 0x7fffffff;
-      for (int rr = lane; rr < nc; rr += 32) {
-        if (mask[rr >> 5] & (1u << (rr & 31))) continue;
-        const float* c = P.Xf + (int64_t)cl[rr] * PP;
-        bool same = true;
-        float d = 0.f;
-        for (int k = 0; k < PP; ++k) {
-          const float t = c[k] - xs[k];
-          same = same && (t == 0.f);
-          d = fmaf(t, t, d);
+    // allowed: not one of this step's ray starts unless it coincides with x*;
+    // if no candidate is allowed, the nearest unselected one (second pair)
+    float xr[PP];
+#pragma unroll
+    for (int k = 0; k < PP; ++k) xr[k] = xs[k];
+    float bd0 = __int_as_float(0x7f800000), bd1 = bd0;
+    int bi0 = 0x7fffffff, bi1 = 0x7fffffff;
+    {
+      const int nw = (nc + 31) >> 5;
+      const uint32_t bit = 1u << lane;
+#pragma unroll 2
+      for (int wd = 0; wd < nw; ++wd) {
+        const int rr = wd * 32 + lane;
+        if (rr < nc && !(mask[wd] & bit)) {
+          const float* c = P.Xf + (int64_t)cl[rr] * PP;
+          bool same = true;
+          float d = 0.f;
+#pragma unroll
+          for (int k = 0; k < PP; k += 4) {
+            const float4 cv = *reinterpret_cast<const float4*>(c + k);
+            float t = cv.x - xr[k]; same &= (t == 0.f); d = fmaf(t, t, d);
+            t = cv.y - xr[k + 1]; same &= (t == 0.f); d = fmaf(t, t, d);
+            t = cv.z - xr[k + 2]; same &= (t == 0.f); d = fmaf(t, t, d);
+            t = cv.w - xr[k + 3]; same &= (t == 0.f); d = fmaf(t, t, d);
+          }
+          if (d < bd1) { bd1 = d; bi1 = rr; }
+          if ((same || !(smask[wd] & bit)) && d < bd0) { bd0 = d; bi0 = rr; }
         }
-        if (pass == 0 && !same) {
-          bool is_start = false;
-          for (int t = 0; t < R; ++t) is_start |= (starts[t] == rr);
-          if (is_start) continue;
-        }
-        if (d < bd) { bd = d; bi = rr; }
       }
-      for (int o = 16; o > 0; o >>= 1) {
-        const float od = __shfl_xor_sync(0xffffffffu, bd, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (od < bd || (od == bd && oi < bi)) { bd = od; bi = oi; }
-      }
-      if (bi != 0x7fffffff) pick = bi;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float od0 = __shfl_xor_sync(0xffffffffu, bd0, o);
+      const int oi0 = __shfl_xor_sync(0xffffffffu, bi0, o);
+      const float od1 = __shfl_xor_sync(0xffffffffu, bd1, o);
+      const int oi1 = __shfl_xor_sync(0xffffffffu, bi1, o);
+      if (od0 < bd0 || (od0 == bd0 && oi0 < bi0)) { bd0 = od0; bi0 = oi0; }
+      if (od1 < bd1 || (od1 == bd1 && oi1 < bi1)) { bd1 = od1; bi1 = oi1; }
+    }
+    const int pick = bi0 != 0x7fffffff ? bi0 : (bi1 != 0x7fffffff ? bi1 : -1);
+    __syncwarp();
+    if (lane < R) smask[starts[lane] >> 5] = 0u;
     if (lane == 0) {
       if (P.tie_gap) P.tie_gap[loc * ldn + (step - P.n0)] =
           (best > 0.f && R > 1) ? (double)((best - second) / best) : 0.0;
