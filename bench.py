@@ -45,6 +45,12 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the other search/precision forms")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle locations (0: 32 per core)")
+    ap.add_argument("--no-batching", action="store_true",
+                    help="skip the uneven-size batching form (persistent kernels, CUDA graph)")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the serving form (request stream over a serving context)")
+    ap.add_argument("--serve-seconds", type=float, default=4.0,
+                    help="arrival window per rate of the serving form")
     return ap.parse_args()
 
 
@@ -280,6 +286,115 @@ def run_extra(args, w, tensors, search, precision, M, steps=2):
             "rmse": rmse}
 
 
+def run_batching(args, steps=3):
+    """Batching form: N = 1e6, p = 8, 50,000 locations with n ~ U{20..100} and
+    N' ~ U{300..2000}; the launch choices autotuned on the first 10,000
+    locations, the whole call captured as one CUDA graph and replayed.  Returns
+    locations/s per search (FP32 scoring, FP64 update)."""
+    import torch
+    from paper_1409_0074_gb300 import lagp
+    from paper_1409_0074_gb300 import workloads as W
+    w = W.uneven_8d(M=50_000)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    X, Y, Xr = (torch.from_numpy(a).to(dev) for a in (w.X, w.Y, w.Xref))
+    nl = torch.from_numpy(w.n_arr.astype(np.int32)).to(dev)
+    ncl = torch.from_numpy(w.nc_arr.astype(np.int32)).to(dev)
+    n, nc = int(w.n_arr.max()), int(w.nc_arr.max())
+    out = {"workload": "sinusoid_8d_N1000000_M50000_uneven", "n": "U{20..100}",
+           "N_close": "U{300..2000}", "nrays": 8}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    for search in ("ray", "exhaustive"):
+        s = lagp.SEARCH[search]
+        wsb = lagp.laGP_workspace_bytes(w.N, w.p, w.M, n, nc, 8, s, lagp.LAGP_FP32_SCORE)
+        ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        mean = torch.empty(w.M, dtype=torch.float64, device=dev)
+        s2 = torch.empty(w.M, dtype=torch.float64, device=dev)
+        Mt = 10_000
+        code = lagp.laGP_autotune(X, Y, Xr[:Mt].contiguous(), w.n0, n, nc, w.theta, w.g, s, 8,
+                                  lagp.LAGP_FP32_SCORE, mean[:Mt], s2[:Mt], ws,
+                                  n_loc=nl[:Mt].contiguous(), nclose_loc=ncl[:Mt].contiguous())
+        plan = lagp.Plan(X, Y, Xr, w.n0, n, nc, w.theta, w.g, s, 8, lagp.LAGP_FP32_SCORE, mean,
+                         s2, ws, n_loc=nl, nclose_loc=ncl)
+        plan.launch(stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            e0.record(stream)
+            plan.launch(stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        rc, st = lagp.laGP_status(ws)
+        if rc != 0:
+            raise RuntimeError("device status %d in the batching form" % st)
+        rmse = float(np.sqrt(np.mean((mean.cpu().numpy() - w.Ytrue) ** 2)))
+        out[search] = {"locations_per_s": w.M * steps / (ms / 1e3), "ms_per_call": ms / steps,
+                       "tune_code": code, "graph": True, "rmse": rmse}
+        plan.close()
+        del ws
+    return out
+
+
+def run_serving(args, rates=(25.0, 50.0, 100.0)):
+    """Serving form: the N = 1e6, p = 8 design resident in a serving context;
+    Poisson request streams at several rates, requests of 1..4096 locations
+    (log-uniform), n in {30, 50, 100}, N' = 1000, ray search, FP32 scoring.
+    Beside it, plain FP64 per-request solves (one request at a time through
+    the host entry, copies included) on a sample of the same requests."""
+    import torch
+    from paper_1409_0074_gb300 import lagp
+    from paper_1409_0074_gb300 import workloads as W
+    from paper_1409_0074_gb300.serve import (CtxBackend, Server, latency_summary,
+                                             poisson_requests, run_stream)
+    w = W.large_8d(M=1)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    X, Y = torch.from_numpy(w.X).to(dev), torch.from_numpy(w.Y).to(dev)
+    slots, max_batch = 8, 4096
+    ctx = lagp.Context(X, Y, w.theta, w.g, w.n0, 1000, lagp.LAGP_RAY, 8, lagp.LAGP_FP32_SCORE,
+                       8 << 30, max_inflight=slots)
+    rng = np.random.default_rng(11)
+    out = {"design": "sinusoid_8d_N1000000", "request_sizes": "log-uniform 1..4096",
+           "n": [30, 50, 100], "N_close": 1000, "search": "ray", "precision": "fp32 scoring",
+           "slots": slots, "max_batch": max_batch, "arena_gb": 8, "rates": []}
+    # warm-up (kernel load, tune table)
+    srv = Server(CtxBackend(ctx, max_batch, slots), max_batch)
+    run_stream(srv, poisson_requests(rng, 200.0, 20, w.p))
+    for rate in rates:
+        reqs = poisson_requests(rng, rate, int(rate * args.serve_seconds), w.p)
+        srv = Server(CtxBackend(ctx, max_batch, slots), max_batch)
+        wall = run_stream(srv, reqs)
+        summ = latency_summary(reqs, wall)
+        summ.update({"rate_per_s": rate, "batches": srv.batches,
+                     "mean_batch": float(np.mean(srv.batch_sizes))})
+        out["rates"].append(summ)
+    ctx.close()
+    # plain FP64 per-request solves: one laGP_build_and_predict call per request,
+    # one at a time, design resident, the request's copies in and out included
+    reqs = poisson_requests(rng, 1.0, 8, w.p)
+    lat, locs = [], 0
+    torch.cuda.synchronize()
+    t_all = time.perf_counter()
+    for r in reqs:
+        t0 = time.perf_counter()
+        xr = torch.from_numpy(r.xref).to(dev)
+        res = lagp.predict(X, Y, xr, w.n0, r.n, 1000, w.theta, w.g, search="ray", nrays=8,
+                           precision="fp64")
+        res["mean"].cpu(), res["s2"].cpu()
+        lat.append(time.perf_counter() - t0)
+        locs += r.xref.shape[0]
+    t_all = time.perf_counter() - t_all
+    lat = np.array(lat) * 1e3
+    out["fp64_per_request"] = {"requests": len(reqs), "locations": locs,
+                               "p50_ms": float(np.percentile(lat, 50)),
+                               "p99_ms": float(np.percentile(lat, 99)),
+                               "locations_per_s": locs / t_all,
+                               "note": "one request at a time (service time, no queueing)"}
+    return out
+
+
 def run_cpu_baseline(args, w, search, sample=None):
     """The FP64 oracle as it stands, OpenMP over locations on the host cores."""
     import oracle
@@ -353,6 +468,10 @@ def main():
             ex["exhaustive_fp64"] = run_extra(args, w, r["tensors"], "exhaustive", "fp64",
                                               min(w.M, 1000), steps=1)
             line["other_forms"] = ex
+        if not args.no_batching:
+            line["batching_form"] = run_batching(args)
+        if not args.no_serving:
+            line["serving_form"] = run_serving(args)
         if not args.no_cpu:
             line["cpu_baseline"] = run_cpu_baseline(args, w, args.search)
     else:

@@ -23,7 +23,10 @@
  *     pointers.  Arrays are dense, row-major, binary64 unless stated.
  *   - The caller owns every buffer.  The library allocates no device memory:
  *     scratch space comes from the caller's `workspace`, sized by
- *     laGP_workspace_bytes.  The library never frees caller memory.
+ *     laGP_workspace_bytes (a serving context sub-allocates from a
+ *     caller-provided arena).  The library never frees caller memory.  Plans
+ *     and serving contexts own CUDA objects (a graph; streams, events and a
+ *     small page-locked status array) until they are destroyed.
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Device entry
  *     points only enqueue work; a return of LAGP_OK means "enqueued".  Errors
  *     found on the device are collected in a status word inside the workspace,
@@ -59,6 +62,7 @@ extern "C" {
 #define LAGP_ERR_WORKSPACE (-2) /* workspace_bytes is below laGP_workspace_bytes */
 #define LAGP_ERR_CUDA (-3)      /* a CUDA call or kernel launch failed */
 #define LAGP_ERR_DEVICE (-4)    /* laGP_status: the device reported a failure */
+#define LAGP_BUSY 1             /* laGP_ctx_submit: no free slot or arena region now */
 
 /* Device status bits reported by laGP_status. */
 #define LAGP_STATUS_TIMEOUT 1u      /* a bounded on-device wait ran out */
@@ -183,6 +187,100 @@ int laGP_build_and_predict_host(const double* design, const double* y, int64_t N
                                 const int32_t* n_loc, const int32_t* nclose_loc, double* mean,
                                 double* s2, int32_t* selected, double* tie_gap, int32_t* nevals,
                                 void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Launch choices (FP32-scoring form).  The persistent kernels have launch
+ * choices that change scheduling only, never a result: locations (warps) per
+ * CTA of the ray kernel (1, 2 or 4), largest-first ordering of uneven work
+ * (n_loc / nclose_loc given), and the fraction of resident CTAs per SM the
+ * exhaustive kernels keep (1 or 1/2).  A process-wide table keyed by
+ * (p, n, N_close, nrays, search, uneven) holds the choice; without an entry
+ * the defaults are 2 warps, largest-first, all resident CTAs.
+ *
+ * laGP_autotune times every choice that applies to these arguments on the
+ * first min(M, chunk) locations (one kNN pass, then for each choice one
+ * untimed and one timed design launch on `stream`), stores the fastest in the
+ * table and returns its code in *choice.  It synchronises `stream` and
+ * overwrites mean and s2.  Arguments as in laGP_build_and_predict.
+ * laGP_tune_get / laGP_tune_set read and install a code for a shape (so a
+ * tuned choice can be saved and restored); `uneven` is 1 for calls with
+ * n_loc or nclose_loc.  Code: ray_warps | lpt << 4 | (exh_occ - 1) << 5.
+ */
+int laGP_autotune(const double* design, const double* y, int64_t N, int p, const double* xref,
+                  int64_t M, int n0, int n, int N_close, double theta, double g, int search,
+                  int nrays, int precision, const int32_t* n_loc, const int32_t* nclose_loc,
+                  double* mean, double* s2, void* workspace, size_t workspace_bytes,
+                  void* stream, int* choice);
+int laGP_tune_get(int p, int n, int N_close, int nrays, int search, int uneven, int* choice);
+int laGP_tune_set(int p, int n, int N_close, int nrays, int search, int uneven, int choice);
+
+/*
+ * Captured plans.  laGP_plan_create records the complete launch sequence of
+ * laGP_build_and_predict for these arguments (same meaning and checks; the
+ * launch choices in force at creation are fixed into the plan) into a CUDA
+ * graph and instantiates it; nothing runs at creation.  laGP_plan_launch
+ * replays it on `stream`: the device reads the buffers behind the pointers
+ * given at creation when the replay runs, so refilling xref (or n_loc,
+ * nclose_loc) in place and launching again predicts at the new contents.
+ * The buffers must stay allocated while the plan exists.  Device status:
+ * laGP_status(workspace, ...) as for a direct call.
+ */
+typedef struct laGP_plan laGP_plan;
+int laGP_plan_create(const double* design, const double* y, int64_t N, int p,
+                     const double* xref, int64_t M, int n0, int n, int N_close, double theta,
+                     double g, int search, int nrays, int precision, const int32_t* n_loc,
+                     const int32_t* nclose_loc, double* mean, double* s2, int32_t* selected,
+                     double* tie_gap, int32_t* nevals, void* workspace, size_t workspace_bytes,
+                     laGP_plan** plan);
+int laGP_plan_launch(laGP_plan* plan, void* stream);
+int laGP_plan_destroy(laGP_plan* plan);
+
+/*
+ * Serving context: a device-resident design and continuous admission of
+ * prediction requests (a deployment form of steps 1-4; the paper's own
+ * implementation is a batch program).
+ *
+ * laGP_ctx_create keeps the device pointers design [N][p] and y [N] (which
+ * must stay valid) with the fixed method settings (theta, g, n0, N_close,
+ * search, nrays, precision), lays out the design part (bounding box, centred
+ * FP32 copy: laGP_ctx_design_bytes(N, p)) at the start of `arena` (device,
+ * 256-byte aligned, arena_bytes long), prepares it (synchronously) and creates
+ * max_inflight (1..64) slots, each with its own stream.
+ *
+ * laGP_ctx_submit admits one request of M locations: xref [M][p] host, an
+ * optional per-location final size n_loc [M] host (each in [n0, n]; NULL:
+ * all n), outputs mean [M], s2 [M] and optionally selected [M][n] (host).  The
+ * request takes a free slot and a first-fit region of the arena of
+ * laGP_ctx_request_bytes(N, p, M, n, N_close, nrays, search, precision,
+ * selected != NULL) bytes; it copies the inputs, enqueues the path on the
+ * slot's stream, queues the copies of the outputs and returns LAGP_OK with a
+ * ticket.  Without a free slot or region it returns LAGP_BUSY and does
+ * nothing.  Host buffers should be page-locked: a pageable output makes the
+ * call wait for the request to finish.  Results of a location do not depend
+ * on the other locations of its request nor on concurrent requests.
+ *
+ * laGP_ctx_poll sets *done = 1 once the request's outputs are in its host
+ * buffers; the first poll that finds it done releases its slot and region and
+ * returns its device status (LAGP_OK or LAGP_ERR_DEVICE); a ticket is
+ * collected once (later polls return LAGP_ERR_INVALID).  laGP_ctx_wait blocks
+ * until the request is done, then polls it.  laGP_ctx_capacity reports the
+ * largest free arena region and the number of free slots.  laGP_ctx_destroy
+ * waits for every slot and releases the context's CUDA objects (the arena is
+ * the caller's).  Calls on one context are serialised by the context.
+ */
+typedef struct laGP_ctx laGP_ctx;
+size_t laGP_ctx_design_bytes(int64_t N, int p);
+size_t laGP_ctx_request_bytes(int64_t N, int p, int64_t M, int n, int N_close, int nrays,
+                              int search, int precision, int want_selected);
+int laGP_ctx_create(const double* design, const double* y, int64_t N, int p, double theta,
+                    double g, int n0, int N_close, int search, int nrays, int precision,
+                    void* arena, size_t arena_bytes, int max_inflight, laGP_ctx** ctx);
+int laGP_ctx_submit(laGP_ctx* ctx, const double* xref, int64_t M, int n, const int32_t* n_loc,
+                    double* mean, double* s2, int32_t* selected, int64_t* ticket);
+int laGP_ctx_poll(laGP_ctx* ctx, int64_t ticket, int* done);
+int laGP_ctx_wait(laGP_ctx* ctx, int64_t ticket);
+int laGP_ctx_capacity(laGP_ctx* ctx, size_t* largest_free, int* free_slots);
+int laGP_ctx_destroy(laGP_ctx* ctx);
 
 /*
  * Opt-in kernel timing.  laGP_profile(1) clears earlier records and makes

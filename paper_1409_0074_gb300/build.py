@@ -26,6 +26,8 @@ UNITS = {
     "lagp_api.cu": [],
     "profile.cu": [],
     "knn_noalloc.cu": [],
+    "schedule.cu": [],
+    "serve.cu": [],
 }
 
 

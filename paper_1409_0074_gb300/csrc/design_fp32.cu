@@ -54,9 +54,12 @@ struct D32Params {
   int32_t* selected;
   double* tie_gap;
   int32_t* nevals;
-  double* Linv;          // [M][n_max][n_max] FP64 inverse factor
-  float* Kc;             // exhaustive: [M][n_max][nc_max] FP32 correlation cache
+  double* Linv;          // [slots][n_max][n_max] FP64 inverse factor
+  float* Kc;             // exhaustive: [slots][n_max][nc_max] FP32 correlation cache
   unsigned* status;
+  unsigned* queue;       // work counter (zero at launch)
+  const int32_t* order;  // item -> location, or null
+  const unsigned* count; // items (device), or null (M)
 };
 
 struct L32 {
@@ -255,14 +258,11 @@ __device__ int search_exh32(const D32Params& P, L32& L, const int32_t* cl, int n
 template <int SEARCH>
 __global__ void __launch_bounds__(D32_THREADS) design32(D32Params P) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int64_t loc = blockIdx.x;
-  if (loc >= P.M) return;
+  __shared__ unsigned s_item;
   const int tid = threadIdx.x, p = P.p, PP = P.PP, ld = P.n_max, R = P.R;
-  const int nc = P.nc_loc ? P.nc_loc[loc] : P.nc_max;
-  const int n = P.n_loc ? P.n_loc[loc] : P.n_max;
-  const int32_t* cl = P.cand + loc * P.nc_max;
-  double* Lg = P.Linv + loc * (int64_t)ld * ld;
-  float* Kc_loc = (SEARCH == 0) ? P.Kc + loc * (int64_t)ld * P.nc_max : nullptr;
+  // scratch of this CTA slot
+  double* Lg = P.Linv + (int64_t)blockIdx.x * ld * ld;
+  float* Kc_loc = (SEARCH == 0) ? P.Kc + (int64_t)blockIdx.x * ld * P.nc_max : nullptr;
 
   L32 L;
   L.ldf = ld | 1;
@@ -297,56 +297,68 @@ __global__ void __launch_bounds__(D32_THREADS) design32(D32Params P) {
   L.rnev = ip; ip += R;
   L.ired = ip; ip += 2 * D32_WARPS + 2;
   L.used = reinterpret_cast<unsigned char*>(ip);
-  L.j = 0;
   L.neg_inv_theta = (float)(-1.0 / P.theta);
   L.onepg = (float)(1.0 + P.g);
+  const unsigned items = P.count ? *P.count : (unsigned)P.M;
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(P.queue, 1u);
+    __syncthreads();
+    const unsigned it = s_item;
+    __syncthreads();
+    if (it >= items) break;
+    const int64_t loc = P.order ? (int64_t)P.order[it] : (int64_t)it;
+    const int nc = P.nc_loc ? P.nc_loc[loc] : P.nc_max;
+    const int n = P.n_loc ? P.n_loc[loc] : P.n_max;
+    const int32_t* cl = P.cand + loc * P.nc_max;
+    L.j = 0;
 
-  for (int r = tid; r < nc; r += blockDim.x) L.used[r] = 0;
-  if (tid < p) L.xq[tid] = P.xref[loc * p + tid];
-  if (tid < PP) {
-    const bool in = tid < p;
-    L.xf[tid] = in ? (float)(P.xref[loc * p + tid] - P.center[tid]) : 0.f;
-    L.lof[tid] = in ? (float)(P.lo[tid] - P.center[tid]) : 0.f;
-    L.hif[tid] = in ? (float)(P.hi[tid] - P.center[tid]) : 0.f;
-  }
-  for (int i = tid; i < ld * L.ldf; i += blockDim.x) L.Lf[i] = 0.f;
-  if (P.tie_gap) for (int i = tid; i < ld; i += blockDim.x) P.tie_gap[loc * ld + i] = 0.0;
-  if (P.nevals) for (int i = tid; i < ld; i += blockDim.x) P.nevals[loc * ld + i] = 0;
-  __syncthreads();
+    for (int r = tid; r < nc; r += blockDim.x) L.used[r] = 0;
+    if (tid < p) L.xq[tid] = P.xref[loc * p + tid];
+    if (tid < PP) {
+      const bool in = tid < p;
+      L.xf[tid] = in ? (float)(P.xref[loc * p + tid] - P.center[tid]) : 0.f;
+      L.lof[tid] = in ? (float)(P.lo[tid] - P.center[tid]) : 0.f;
+      L.hif[tid] = in ? (float)(P.hi[tid] - P.center[tid]) : 0.f;
+    }
+    for (int i = tid; i < ld * L.ldf; i += blockDim.x) L.Lf[i] = 0.f;
+    if (P.tie_gap) for (int i = tid; i < ld; i += blockDim.x) P.tie_gap[loc * ld + i] = 0.0;
+    if (P.nevals) for (int i = tid; i < ld; i += blockDim.x) P.nevals[loc * ld + i] = 0;
+    __syncthreads();
 
-  bool ok = (n >= P.n0) && (n <= nc) && (n <= ld);
-  for (int r = 0; r < P.n0 && ok; ++r) ok = add_point32<SEARCH>(P, L, cl, nc, r, Lg, Kc_loc);
-  for (int j = P.n0; j < n && ok; ++j) {
-    double gap = 0.0;
-    int ne = 0;
-    int r = search_exh32(P, L, cl, nc, Kc_loc, &gap);
-    if (tid == 0) {
-      if (P.tie_gap) P.tie_gap[loc * ld + (j - P.n0)] = gap;
-      if (P.nevals) P.nevals[loc * ld + (j - P.n0)] = ne;
+    bool ok = (n >= P.n0) && (n <= nc) && (n <= ld);
+    for (int r = 0; r < P.n0 && ok; ++r) ok = add_point32<SEARCH>(P, L, cl, nc, r, Lg, Kc_loc);
+    for (int j = P.n0; j < n && ok; ++j) {
+      double gap = 0.0;
+      int ne = 0;
+      int r = search_exh32(P, L, cl, nc, Kc_loc, &gap);
+      if (tid == 0) {
+        if (P.tie_gap) P.tie_gap[loc * ld + (j - P.n0)] = gap;
+        if (P.nevals) P.nevals[loc * ld + (j - P.n0)] = ne;
+      }
+      ok = (r >= 0) && add_point32<SEARCH>(P, L, cl, nc, r, Lg, Kc_loc);
     }
-    ok = (r >= 0) && add_point32<SEARCH>(P, L, cl, nc, r, Lg, Kc_loc);
+    if (ok) {
+      double a = 0.0, b = 0.0, c = 0.0, dmy = 0.0;
+      for (int i = tid; i < L.j; i += blockDim.x) {
+        a = fma(L.z[i], L.zy[i], a);
+        b = fma(L.zy[i], L.zy[i], b);
+        c = fma(L.z[i], L.z[i], c);
+      }
+      block_sum2(a, b, L.dred);
+      block_sum2(c, dmy, L.dred);
+      if (tid == 0) {
+        P.mean[loc] = a;
+        P.s2[loc] = b * ((1.0 + P.g) - c) / (double)L.j;
+      }
+    } else if (tid == 0) {
+      P.mean[loc] = __longlong_as_double(0x7ff8000000000000ll);
+      P.s2[loc] = __longlong_as_double(0x7ff8000000000000ll);
+      atomicOr(P.status, LAGP_DEV_BAD_UPDATE);
+    }
+    if (P.selected)
+      for (int i = tid; i < ld; i += blockDim.x)
+        P.selected[loc * ld + i] = (i < L.j) ? cl[L.sel[i]] : -1;
   }
-  if (ok) {
-    double a = 0.0, b = 0.0, c = 0.0, dmy = 0.0;
-    for (int i = tid; i < L.j; i += blockDim.x) {
-      a = fma(L.z[i], L.zy[i], a);
-      b = fma(L.zy[i], L.zy[i], b);
-      c = fma(L.z[i], L.z[i], c);
-    }
-    block_sum2(a, b, L.dred);
-    block_sum2(c, dmy, L.dred);
-    if (tid == 0) {
-      P.mean[loc] = a;
-      P.s2[loc] = b * ((1.0 + P.g) - c) / (double)L.j;
-    }
-  } else if (tid == 0) {
-    P.mean[loc] = __longlong_as_double(0x7ff8000000000000ll);
-    P.s2[loc] = __longlong_as_double(0x7ff8000000000000ll);
-    atomicOr(P.status, LAGP_DEV_BAD_UPDATE);
-  }
-  if (P.selected)
-    for (int i = tid; i < ld; i += blockDim.x)
-      P.selected[loc * ld + i] = (i < L.j) ? cl[L.sel[i]] : -1;
 }
 
 static size_t smem_design32(int n_max, int p, int PP, int nc_max, int R, int search) {
@@ -359,9 +371,7 @@ static size_t smem_design32(int n_max, int p, int PP, int nc_max, int R, int sea
   return d * 8 + f * 4 + i * 4 + nc_max + 16;
 }
 
-cudaError_t launch_design_fp32(const DesignArgs& a, int search, cudaStream_t s) {
-  if (search != 0) return launch_ray32(a, s);
-  if (exh_tc_supported(a.n_max)) return launch_exh_tc(a, s);
+cudaError_t launch_exh32(const DesignArgs& a, cudaStream_t s) {
   D32Params P;
   P.X = a.X; P.Y = a.Y; P.p = a.p; P.PP = a.PP; P.Xf = a.ws->Xf; P.xref = a.xref; P.M = a.M;
   P.cand = a.cand; P.nc_max = a.nc_max; P.nc_loc = a.nc_loc; P.n0 = a.n0; P.n_max = a.n_max;
@@ -369,12 +379,17 @@ cudaError_t launch_design_fp32(const DesignArgs& a, int search, cudaStream_t s) 
   P.hi = a.ws->hi; P.center = a.ws->center; P.mean = a.mean; P.s2 = a.s2;
   P.selected = a.selected; P.tie_gap = a.tie_gap; P.nevals = a.nevals; P.Linv = a.ws->state64;
   P.Kc = a.ws->state32; P.status = a.ws->status;
+  P.queue = a.ws->queue + 2; P.order = a.order; P.count = a.count;
   size_t sm = smem_design32(a.n_max, a.p, a.PP, a.nc_max, a.nrays, 0);
   cudaError_t err =
       cudaFuncSetAttribute(design32<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (err != cudaSuccess) return err;
+  const int64_t grid = persistent_grid(design32<0>, D32_THREADS, sm, a.M, exh_slots(a.ws->chunk), 1,
+                                       a.tune.exh_occ);
+  if (grid < 0) return cudaErrorInvalidValue;
+  if ((err = cudaMemsetAsync(P.queue, 0, sizeof(unsigned), s)) != cudaSuccess) return err;
   prof_begin("design32_exhaustive", s);
-  design32<0><<<(unsigned)a.M, D32_THREADS, sm, s>>>(P);
+  design32<0><<<(unsigned)grid, D32_THREADS, sm, s>>>(P);
   prof_end(s);
   return cudaGetLastError();
 }

@@ -49,9 +49,12 @@ struct XtParams {
   int32_t* selected;
   double* tie_gap;
   int32_t* nevals;
-  double* Linv;          // [M][n_max][n_max]
-  float* Kc;             // [M][n_max][nc_max]
+  double* Linv;          // [slots][n_max][n_max]
+  float* Kc;             // [slots][n_max][nc_max]
   unsigned* status;
+  unsigned* queue;       // work counter (zero at launch)
+  const int32_t* order;  // item -> location, or null
+  const unsigned* count; // items (device), or null (M)
 };
 
 // canonical no-swizzle K-major layout with XT_KMAX columns per row
@@ -123,7 +126,10 @@ __global__ void __launch_bounds__(XT_THREADS) exh_tc_kernel(XtParams P) {
   float* Blo = Bhi + XtSmem::B_BYTES / 4;
   float* Ahi = reinterpret_cast<float*>(smem + XtSmem::A_OFF);
   float* Alo = Ahi + XtSmem::A_BYTES / 4;
-  const int p = P.p, PP = P.PP, ld = P.n_max, nc_max = P.nc_max;
+  // ld: row stride of the slot's L^{-1} (the part of a mixed launch that runs
+  // here has n <= XT_KMAX); ldo: row stride of the per-step outputs
+  const int p = P.p, PP = P.PP, ldo = P.n_max, nc_max = P.nc_max;
+  const int ld = ldo < XT_KMAX ? ldo : XT_KMAX;
   // small state after the operands
   float* kap = reinterpret_cast<float*>(smem + XtSmem::END);          // [nc_max]
   float* zf = kap + ((nc_max + 3) & ~3);                             // [XT_KMAX]
@@ -142,30 +148,8 @@ __global__ void __launch_bounds__(XT_THREADS) exh_tc_kernel(XtParams P) {
       (reinterpret_cast<uintptr_t>(used + nc_max) + 15) & ~(uintptr_t)15);
   uint32_t* tbase = reinterpret_cast<uint32_t*>(bar + 1);
 
-  const int64_t loc = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nc = P.nc_loc ? P.nc_loc[loc] : nc_max;
-  const int n = P.n_loc ? P.n_loc[loc] : P.n_max;
-  const int32_t* cl = P.cand + loc * nc_max;
-  double* Lg = P.Linv + loc * (int64_t)ld * ld;
-  float* Kc = P.Kc + loc * (int64_t)ld * nc_max;
-  const double* xq = P.xref + loc * p;
-  const float nit = (float)(-1.0 / P.theta);
-  const float onepg = (float)(1.0 + P.g);
-
-  for (int i = tid; i < 2 * XtSmem::B_BYTES / 4; i += XT_THREADS) Bhi[i] = 0.f;
-  for (int r = tid; r < nc; r += XT_THREADS) {
-    used[r] = 0;
-    const float* c = P.Xf + (int64_t)cl[r] * PP;
-    float d = 0.f;
-    for (int k = 0; k < p; ++k) {
-      const float t = c[k] - (float)(xq[k] - P.center[k]);
-      d = fmaf(t, t, d);
-    }
-    kap[r] = __expf(d * nit);
-  }
-  if (P.tie_gap) for (int i = tid; i < ld; i += XT_THREADS) P.tie_gap[loc * ld + i] = 0.0;
-  if (P.nevals) for (int i = tid; i < ld; i += XT_THREADS) P.nevals[loc * ld + i] = 0;
+  unsigned* s_item = tbase + 1;
   if (tid == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
@@ -179,198 +163,233 @@ __global__ void __launch_bounds__(XT_THREADS) exh_tc_kernel(XtParams P) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t taddr = *tbase;
-
-  int j = 0;
+  // scratch of this CTA slot
+  double* Lg = P.Linv + (int64_t)blockIdx.x * ld * ld;
+  float* Kc = P.Kc + (int64_t)blockIdx.x * ld * nc_max;
+  const float nit = (float)(-1.0 / P.theta);
+  const float onepg = (float)(1.0 + P.g);
+  const unsigned items = P.count ? *P.count : (unsigned)P.M;
   uint32_t phase = 0;
-  bool ok = (n >= P.n0) && (n <= nc) && (n <= ld) && (ld <= XT_KMAX);
+  bool timed_out = false;
+  while (!timed_out) {
+    if (tid == 0) *s_item = atomicAdd(P.queue, 1u);
+    __syncthreads();
+    const unsigned it = *s_item;
+    __syncthreads();
+    if (it >= items) break;
+    const int64_t loc = P.order ? (int64_t)P.order[it] : (int64_t)it;
+    const int nc = P.nc_loc ? P.nc_loc[loc] : nc_max;
+    const int n = P.n_loc ? P.n_loc[loc] : P.n_max;
+    const int32_t* cl = P.cand + loc * nc_max;
+    const double* xq = P.xref + loc * p;
 
-  // ---- append candidate rank rr: FP64 factor row, z, L^{-1}y, B row, Kc row ----
-  auto add_point = [&](int rr) -> bool {
-    const double* c = P.X + (int64_t)cl[rr] * p;
-    if (tid < p) S64[j * p + tid] = c[tid];
-    __syncthreads();
-    for (int i = tid; i < j; i += XT_THREADS) kv[i] = corr64(S64 + i * p, S64 + j * p, p, P.theta);
-    __syncthreads();
-    double vv = 0.0;
-    for (int i = tid; i < j; i += XT_THREADS) {
-      const double* Li = Lg + (int64_t)i * ld;
-      double acc = 0.0;
-      for (int k = 0; k <= i; ++k) acc = fma(Li[k], kv[k], acc);
-      lv[i] = acc;
-      vv = fma(acc, acc, vv);
+    for (int i = tid; i < 2 * XtSmem::B_BYTES / 4; i += XT_THREADS) Bhi[i] = 0.f;
+    for (int r = tid; r < nc; r += XT_THREADS) {
+      used[r] = 0;
+      const float* c = P.Xf + (int64_t)cl[r] * PP;
+      float d = 0.f;
+      for (int k = 0; k < p; ++k) {
+        const float t = c[k] - (float)(xq[k] - P.center[k]);
+        d = fmaf(t, t, d);
+      }
+      kap[r] = __expf(d * nit);
     }
-    vv = xsum(vv, red);
-    const double v = (1.0 + P.g) - vv;
-    if (!(v > 0.0)) return false;
-    const double inv_d = 1.0 / sqrt(v);
-    for (int k = tid; k <= j; k += XT_THREADS) {
-      double rk = inv_d;
-      if (k < j) {
+    if (P.tie_gap) for (int i = tid; i < ldo; i += XT_THREADS) P.tie_gap[loc * ldo + i] = 0.0;
+    if (P.nevals) for (int i = tid; i < ldo; i += XT_THREADS) P.nevals[loc * ldo + i] = 0;
+    __syncthreads();
+
+    int j = 0;
+    bool ok = (n >= P.n0) && (n <= nc) && (n <= ld);
+
+    // ---- append candidate rank rr: FP64 factor row, z, L^{-1}y, B row, Kc row ----
+    auto add_point = [&](int rr) -> bool {
+      const double* c = P.X + (int64_t)cl[rr] * p;
+      if (tid < p) S64[j * p + tid] = c[tid];
+      __syncthreads();
+      for (int i = tid; i < j; i += XT_THREADS) kv[i] = corr64(S64 + i * p, S64 + j * p, p, P.theta);
+      __syncthreads();
+      double vv = 0.0;
+      for (int i = tid; i < j; i += XT_THREADS) {
+        const double* Li = Lg + (int64_t)i * ld;
         double acc = 0.0;
-        for (int i = k; i < j; ++i) acc = fma(lv[i], Lg[(int64_t)i * ld + k], acc);
-        rk = -acc * inv_d;
+        for (int k = 0; k <= i; ++k) acc = fma(Li[k], kv[k], acc);
+        lv[i] = acc;
+        vv = fma(acc, acc, vv);
       }
-      Lg[(int64_t)j * ld + k] = rk;
-      const float h = xtf32((float)rk);
-      const uint32_t off = xcanon(j, k) >> 2;
-      Bhi[off] = h;
-      Blo[off] = xtf32((float)(rk - (double)h));
-    }
-    if (tid == 0) {
-      kx[j] = corr64(S64 + j * p, xq, p, P.theta);
-      sel[j] = rr;
-      used[rr] = 1;
-    }
-    __syncthreads();
-    double zz = 0.0, zyy = 0.0;
-    for (int k = tid; k <= j; k += XT_THREADS) {
-      const double rk = Lg[(int64_t)j * ld + k];
-      zz = fma(rk, kx[k], zz);
-      zyy = fma(rk, P.Y[cl[sel[k]]], zyy);
-    }
-    zz = xsum(zz, red);
-    zyy = xsum(zyy, red);
-    if (tid == 0) {
-      z[j] = zz;
-      zy[j] = zyy;
-      zf[j] = (float)zz;
-    }
-    // correlation cache row j: K(c_r, S_j) for every candidate
-    const float* sj = P.Xf + (int64_t)cl[rr] * PP;
-    for (int q = tid; q < nc; q += XT_THREADS)
-      Kc[(int64_t)j * nc_max + q] = __expf(sqdist_row32(P.Xf + (int64_t)cl[q] * PP, sj, PP) * nit);
-    __syncthreads();
-    ++j;
-    return true;
-  };
-
-  for (int rr = 0; rr < P.n0 && ok; ++rr) ok = add_point(rr);
-
-  for (int step = P.n0; step < n && ok; ++step) {
-    const int jn = (j + 15) & ~15;       // N of the MMA
-    const int jk = (j + 7) & ~7;         // K of the MMA
-    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(jn >> 3) << 17) |
-                           ((uint32_t)(128 >> 4) << 24);
-    float best = -1.f, second = -1.f;
-    int bi = -1;
-    for (int base = 0; base < nc; base += 128) {
-      // A operand: this thread's candidate row, hi / lo, zero past j
-      const int r = base + tid;
-      const bool live = r < nc;
-#pragma unroll 4
-      for (int k = 0; k < jk; k += 4) {
-        float4 h, l;
-        float vals[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          vals[u] = (live && k + u < j) ? Kc[(int64_t)(k + u) * nc_max + r] : 0.f;
-        h.x = xtf32(vals[0]); h.y = xtf32(vals[1]); h.z = xtf32(vals[2]); h.w = xtf32(vals[3]);
-        l.x = xtf32(vals[0] - h.x); l.y = xtf32(vals[1] - h.y);
-        l.z = xtf32(vals[2] - h.z); l.w = xtf32(vals[3] - h.w);
-        const uint32_t off = xcanon(tid, k) >> 2;
-        *reinterpret_cast<float4*>(Ahi + off) = h;
-        *reinterpret_cast<float4*>(Alo + off) = l;
+      vv = xsum(vv, red);
+      const double v = (1.0 + P.g) - vv;
+      if (!(v > 0.0)) return false;
+      const double inv_d = 1.0 / sqrt(v);
+      for (int k = tid; k <= j; k += XT_THREADS) {
+        double rk = inv_d;
+        if (k < j) {
+          double acc = 0.0;
+          for (int i = k; i < j; ++i) acc = fma(lv[i], Lg[(int64_t)i * ld + k], acc);
+          rk = -acc * inv_d;
+        }
+        Lg[(int64_t)j * ld + k] = rk;
+        const float h = xtf32((float)rk);
+        const uint32_t off = xcanon(j, k) >> 2;
+        Bhi[off] = h;
+        Blo[off] = xtf32((float)(rk - (double)h));
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      if (tid == 0) {
+        kx[j] = corr64(S64 + j * p, xq, p, P.theta);
+        sel[j] = rr;
+        used[rr] = 1;
+      }
+      __syncthreads();
+      double zz = 0.0, zyy = 0.0;
+      for (int k = tid; k <= j; k += XT_THREADS) {
+        const double rk = Lg[(int64_t)j * ld + k];
+        zz = fma(rk, kx[k], zz);
+        zyy = fma(rk, P.Y[cl[sel[k]]], zyy);
+      }
+      zz = xsum(zz, red);
+      zyy = xsum(zyy, red);
+      if (tid == 0) {
+        z[j] = zz;
+        zy[j] = zyy;
+        zf[j] = (float)zz;
+      }
+      // correlation cache row j: K(c_r, S_j) for every candidate
+      const float* sj = P.Xf + (int64_t)cl[rr] * PP;
+      for (int q = tid; q < nc; q += XT_THREADS)
+        Kc[(int64_t)j * nc_max + q] = __expf(sqdist_row32(P.Xf + (int64_t)cl[q] * PP, sj, PP) * nit);
+      __syncthreads();
+      ++j;
+      return true;
+    };
+
+    for (int rr = 0; rr < P.n0 && ok; ++rr) ok = add_point(rr);
+
+    for (int step = P.n0; step < n && ok; ++step) {
+      const int jn = (j + 15) & ~15;       // N of the MMA
+      const int jk = (j + 7) & ~7;         // K of the MMA
+      const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(jn >> 3) << 17) |
+                             ((uint32_t)(128 >> 4) << 24);
+      float best = -1.f, second = -1.f;
+      int bi = -1;
+      for (int base = 0; base < nc; base += 128) {
+        // A operand: this thread's candidate row, hi / lo, zero past j
+        const int r = base + tid;
+        const bool live = r < nc;
+  #pragma unroll 4
+        for (int k = 0; k < jk; k += 4) {
+          float4 h, l;
+          float vals[4];
+  #pragma unroll
+          for (int u = 0; u < 4; ++u)
+            vals[u] = (live && k + u < j) ? Kc[(int64_t)(k + u) * nc_max + r] : 0.f;
+          h.x = xtf32(vals[0]); h.y = xtf32(vals[1]); h.z = xtf32(vals[2]); h.w = xtf32(vals[3]);
+          l.x = xtf32(vals[0] - h.x); l.y = xtf32(vals[1] - h.y);
+          l.z = xtf32(vals[2] - h.z); l.w = xtf32(vals[3] - h.w);
+          const uint32_t off = xcanon(tid, k) >> 2;
+          *reinterpret_cast<float4*>(Ahi + off) = h;
+          *reinterpret_cast<float4*>(Alo + off) = l;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo);
+          const uint32_t bh = smem_u32(Bhi), bl = smem_u32(Blo);
+          for (int ks = 0; ks < jk / 8; ++ks) {
+            const uint32_t ko = ks * 256;
+            xmma(taddr, xdesc(ah + ko), xdesc(bh + ko), idesc, ks > 0 ? 1u : 0u);
+            xmma(taddr, xdesc(ah + ko), xdesc(bl + ko), idesc, 1u);
+            xmma(taddr, xdesc(al + ko), xdesc(bh + ko), idesc, 1u);
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(bar))
+                       : "memory");
+        }
+        bool done = mbar_wait(bar, phase);
+        phase ^= 1u;
+        if (!__syncthreads_and(done)) {
+          if (tid == 0) atomicOr(P.status, LAGP_DEV_TIMEOUT);
+          ok = false;
+          timed_out = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // epilogue: row tid of W
+        float vs = 0.f, ns = 0.f;
+        const uint32_t row = taddr + ((uint32_t)(warp * 32) << 16);
+        for (int c0 = 0; c0 < jn; c0 += 16) {
+          float w[16];
+          xld16(row + c0, w);
+  #pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            const int i = c0 + u;
+            const float wi = i < j ? w[u] : 0.f;
+            vs = fmaf(wi, wi, vs);
+            ns = fmaf(wi, i < j ? zf[i] : 0.f, ns);
+          }
+        }
+        if (live && !used[r]) {
+          const float v = onepg - vs;
+          const float num = ns - kap[r];
+          const float alc = v > 0.f ? num * num / v : 0.f;
+          if (alc > best) { second = best; best = alc; bi = r; }
+          else if (alc > second) second = alc;
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+      }
+      if (!ok) break;
+      // block argmax, ties to the lower rank; the second best for the gap
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const float os = __shfl_xor_sync(0xffffffffu, second, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi >= 0 && (bi < 0 || oi < bi))) {
+          second = fmaxf(best, os); best = ob; bi = oi;
+        } else {
+          second = fmaxf(second, ob);
+        }
+      }
+      if (lane == 0) { fred[2 * warp] = best; fred[2 * warp + 1] = second; ired[warp] = bi; }
       __syncthreads();
       if (tid == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo);
-        const uint32_t bh = smem_u32(Bhi), bl = smem_u32(Blo);
-        for (int ks = 0; ks < jk / 8; ++ks) {
-          const uint32_t ko = ks * 256;
-          xmma(taddr, xdesc(ah + ko), xdesc(bh + ko), idesc, ks > 0 ? 1u : 0u);
-          xmma(taddr, xdesc(ah + ko), xdesc(bl + ko), idesc, 1u);
-          xmma(taddr, xdesc(al + ko), xdesc(bh + ko), idesc, 1u);
+        float b = fred[0], s = fred[1];
+        int ii = ired[0];
+        for (int w = 1; w < XT_THREADS / 32; ++w) {
+          const float ob = fred[2 * w], os = fred[2 * w + 1];
+          const int oi = ired[w];
+          if (ob > b || (ob == b && oi >= 0 && (ii < 0 || oi < ii))) { s = fmaxf(b, os); b = ob; ii = oi; }
+          else s = fmaxf(s, ob);
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(bar))
-                     : "memory");
+        ired[4] = ii;
+        if (P.tie_gap) P.tie_gap[loc * ldo + (step - P.n0)] = (b > 0.f && s >= 0.f) ? (double)((b - s) / b) : 0.0;
       }
-      bool done = mbar_wait(bar, phase);
-      phase ^= 1u;
-      if (!__syncthreads_and(done)) {
-        if (tid == 0) atomicOr(P.status, LAGP_DEV_TIMEOUT);
-        ok = false;
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // epilogue: row tid of W
-      float vs = 0.f, ns = 0.f;
-      const uint32_t row = taddr + ((uint32_t)(warp * 32) << 16);
-      for (int c0 = 0; c0 < jn; c0 += 16) {
-        float w[16];
-        xld16(row + c0, w);
-#pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          const int i = c0 + u;
-          const float wi = i < j ? w[u] : 0.f;
-          vs = fmaf(wi, wi, vs);
-          ns = fmaf(wi, i < j ? zf[i] : 0.f, ns);
-        }
-      }
-      if (live && !used[r]) {
-        const float v = onepg - vs;
-        const float num = ns - kap[r];
-        const float alc = v > 0.f ? num * num / v : 0.f;
-        if (alc > best) { second = best; best = alc; bi = r; }
-        else if (alc > second) second = alc;
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncthreads();
+      const int pick = ired[4];
+      ok = (pick >= 0) && add_point(pick);
     }
-    if (!ok) break;
-    // block argmax, ties to the lower rank; the second best for the gap
-    for (int o = 16; o > 0; o >>= 1) {
-      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-      const float os = __shfl_xor_sync(0xffffffffu, second, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ob > best || (ob == best && oi >= 0 && (bi < 0 || oi < bi))) {
-        second = fmaxf(best, os); best = ob; bi = oi;
-      } else {
-        second = fmaxf(second, ob);
-      }
-    }
-    if (lane == 0) { fred[2 * warp] = best; fred[2 * warp + 1] = second; ired[warp] = bi; }
-    __syncthreads();
-    if (tid == 0) {
-      float b = fred[0], s = fred[1];
-      int ii = ired[0];
-      for (int w = 1; w < XT_THREADS / 32; ++w) {
-        const float ob = fred[2 * w], os = fred[2 * w + 1];
-        const int oi = ired[w];
-        if (ob > b || (ob == b && oi >= 0 && (ii < 0 || oi < ii))) { s = fmaxf(b, os); b = ob; ii = oi; }
-        else s = fmaxf(s, ob);
-      }
-      ired[4] = ii;
-      if (P.tie_gap) P.tie_gap[loc * ld + (step - P.n0)] = (b > 0.f && s >= 0.f) ? (double)((b - s) / b) : 0.0;
-    }
-    __syncthreads();
-    const int pick = ired[4];
-    ok = (pick >= 0) && add_point(pick);
-  }
 
-  if (ok) {
-    double a = 0.0, b = 0.0, c = 0.0;
-    for (int i = tid; i < j; i += XT_THREADS) {
-      a = fma(z[i], zy[i], a);
-      b = fma(zy[i], zy[i], b);
-      c = fma(z[i], z[i], c);
+    if (ok) {
+      double a = 0.0, b = 0.0, c = 0.0;
+      for (int i = tid; i < j; i += XT_THREADS) {
+        a = fma(z[i], zy[i], a);
+        b = fma(zy[i], zy[i], b);
+        c = fma(z[i], z[i], c);
+      }
+      a = xsum(a, red);
+      b = xsum(b, red);
+      c = xsum(c, red);
+      if (tid == 0) {
+        P.mean[loc] = a;
+        P.s2[loc] = b * ((1.0 + P.g) - c) / (double)j;
+      }
+    } else if (tid == 0) {
+      P.mean[loc] = __longlong_as_double(0x7ff8000000000000ll);
+      P.s2[loc] = __longlong_as_double(0x7ff8000000000000ll);
+      atomicOr(P.status, LAGP_DEV_BAD_UPDATE);
     }
-    a = xsum(a, red);
-    b = xsum(b, red);
-    c = xsum(c, red);
-    if (tid == 0) {
-      P.mean[loc] = a;
-      P.s2[loc] = b * ((1.0 + P.g) - c) / (double)j;
-    }
-  } else if (tid == 0) {
-    P.mean[loc] = __longlong_as_double(0x7ff8000000000000ll);
-    P.s2[loc] = __longlong_as_double(0x7ff8000000000000ll);
-    atomicOr(P.status, LAGP_DEV_BAD_UPDATE);
+    if (P.selected)
+      for (int i = tid; i < ldo; i += XT_THREADS) P.selected[loc * ldo + i] = (i < j) ? cl[sel[i]] : -1;
   }
-  if (P.selected)
-    for (int i = tid; i < ld; i += XT_THREADS) P.selected[loc * ld + i] = (i < j) ? cl[sel[i]] : -1;
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
@@ -379,7 +398,7 @@ __global__ void __launch_bounds__(XT_THREADS) exh_tc_kernel(XtParams P) {
   }
 }
 
-bool exh_tc_supported(int n_max) { return n_max <= XT_KMAX; }
+int exh_tc_max_n() { return XT_KMAX; }
 
 cudaError_t launch_exh_tc(const DesignArgs& a, cudaStream_t s) {
   XtParams P;
@@ -388,14 +407,19 @@ cudaError_t launch_exh_tc(const DesignArgs& a, cudaStream_t s) {
   P.n_loc = a.n_loc; P.theta = a.theta; P.g = a.g; P.center = a.ws->center; P.mean = a.mean;
   P.s2 = a.s2; P.selected = a.selected; P.tie_gap = a.tie_gap; P.nevals = a.nevals;
   P.Linv = a.ws->state64; P.Kc = a.ws->state32; P.status = a.ws->status;
+  P.queue = a.ws->queue + 1; P.order = a.order; P.count = a.count;
   const size_t small = (size_t)((a.nc_max + 3) & ~3) * 4 + XT_KMAX * 4 + (size_t)XT_KMAX * a.p * 8 +
                        5 * XT_KMAX * 8 + 8 * 8 + 8 * 4 + 8 * 4 + XT_KMAX * 4 + a.nc_max + 64;
   const size_t sm = 1024 + XtSmem::END + small;
   cudaError_t err =
       cudaFuncSetAttribute(exh_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (err != cudaSuccess) return err;
+  const int64_t grid = persistent_grid(exh_tc_kernel, XT_THREADS, sm, a.M, exh_slots(a.ws->chunk), 1,
+                                       a.tune.exh_occ);
+  if (grid < 0) return cudaErrorInvalidValue;
+  if ((err = cudaMemsetAsync(P.queue, 0, sizeof(unsigned), s)) != cudaSuccess) return err;
   prof_begin("exh_tc", s);
-  exh_tc_kernel<<<(unsigned)a.M, XT_THREADS, sm, s>>>(P);
+  exh_tc_kernel<<<(unsigned)grid, XT_THREADS, sm, s>>>(P);
   prof_end(s);
   return cudaGetLastError();
 }

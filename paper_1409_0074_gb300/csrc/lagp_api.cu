@@ -14,55 +14,83 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // candidate buffers within 16 GiB.
 static int64_t chunk_for(int64_t M, int search, int precision, int nc_max, int64_t N) {
   int64_t cap = 131072;
-  if (search == LAGP_EXHAUSTIVE) cap = (precision == LAGP_FP64) ? 16384 : 32768;
+  if (search == LAGP_EXHAUSTIVE && precision == LAGP_FP64) cap = 16384;
   const int64_t per_loc = (int64_t)8 * knn_cap(nc_max);
   const int64_t by_mem = ((int64_t)16 << 30) / per_loc;
   if (by_mem < cap) cap = by_mem > 128 ? by_mem : 128;
   return M < cap ? (M > 0 ? M : 1) : cap;
 }
 
-size_t layout_workspace(const Shape& sh, void* base, Workspace* ws) {
-  size_t off = 0;
-  char* b = static_cast<char*>(base);
-  auto take = [&](size_t bytes) -> void* {
+namespace {
+struct Carver {
+  char* b;
+  size_t off;
+  void* take(size_t bytes) {
     void* ptr = b ? b + off : nullptr;
     off += align256(bytes);
     return ptr;
-  };
-  Workspace w;
-  std::memset(&w, 0, sizeof(w));
-  unsigned* words = static_cast<unsigned*>(take(2 * sizeof(unsigned)));
-  w.status = words;
-  w.maxn2 = words ? words + 1 : nullptr;
-  w.bbox_part = static_cast<double*>(take(sizeof(double) * 64 * 2 * sh.p));
-  w.lo = static_cast<double*>(take(sizeof(double) * sh.p));
-  w.hi = static_cast<double*>(take(sizeof(double) * sh.p));
-  w.center = static_cast<double*>(take(sizeof(double) * sh.p));
-  w.Xf = static_cast<float*>(take(sizeof(float) * sh.Npad * sh.PP));
-  w.nx = static_cast<float*>(take(sizeof(float) * sh.Npad));
-  const int64_t c = sh.chunk;
-  w.knn_buf = take((size_t)8 * c * knn_cap(sh.nc_max));
-  w.knn_cnt = static_cast<int32_t*>(take(sizeof(int32_t) * c));
-  w.cand = static_cast<int32_t*>(take(sizeof(int32_t) * c * sh.nc_max));
+  }
+};
+}  // namespace
+
+// Per-request part: the status word first (laGP_status reads it there), then
+// the kNN buffers, candidates, per-slot scratch and the work order.
+size_t layout_request(const Shape& sh, void* base, Workspace* ws) {
+  Workspace scratch;
+  Workspace* w = ws ? ws : &scratch;   // sizes only when ws is null
+  Carver c{static_cast<char*>(base), 0};
+  w->status = static_cast<unsigned*>(c.take(4 * sizeof(unsigned)));
+  const int64_t ch = sh.chunk;
+  w->knn_buf = c.take((size_t)8 * ch * knn_cap(sh.nc_max));
+  w->knn_cnt = static_cast<int32_t*>(c.take(sizeof(int32_t) * ch));
+  w->cand = static_cast<int32_t*>(c.take(sizeof(int32_t) * ch * sh.nc_max));
   size_t s64 = 0, s32 = 0;
   if (sh.precision == LAGP_FP64) {
-    if (sh.search == LAGP_EXHAUSTIVE) s64 = sizeof(double) * c * sh.n_max * sh.nc_max;
+    if (sh.search == LAGP_EXHAUSTIVE) s64 = sizeof(double) * ch * sh.n_max * sh.nc_max;
+  } else if (sh.search == LAGP_RAY) {
+    s64 = sizeof(double) * ray32_slots(ch) * ray32_g64_doubles(sh.n_max);
   } else {
-    const size_t per = (size_t)sh.n_max * sh.n_max > ray32_g64_doubles(sh.n_max)
-                           ? (size_t)sh.n_max * sh.n_max
-                           : ray32_g64_doubles(sh.n_max);
-    s64 = sizeof(double) * c * per;
-    if (sh.search == LAGP_EXHAUSTIVE) s32 = sizeof(float) * c * sh.n_max * sh.nc_max;
+    const size_t slots = exh_slots(ch);
+    s64 = sizeof(double) * slots * sh.n_max * sh.n_max;
+    s32 = sizeof(float) * slots * sh.n_max * sh.nc_max;
   }
-  w.state64 = static_cast<double*>(take(s64));
-  w.state32 = static_cast<float*>(take(s32));
-  w.chunk = c;
-  if (ws) *ws = w;
-  return off;
+  w->state64 = static_cast<double*>(c.take(s64));
+  w->state32 = static_cast<float*>(c.take(s32));
+  w->queue = static_cast<unsigned*>(c.take(4 * sizeof(unsigned)));
+  w->order = static_cast<int32_t*>(c.take(sizeof(int32_t) * 2 * ch));
+  w->order_hist = static_cast<unsigned*>(c.take(512 * sizeof(unsigned)));
+  w->order_count = static_cast<unsigned*>(c.take(2 * sizeof(unsigned)));
+  w->order_key = static_cast<uint16_t*>(c.take(sizeof(uint16_t) * ch));
+  w->chunk = ch;
+  return c.off;
 }
 
-static bool make_shape(int64_t N, int p, int64_t M, int n0, int n, int N_close, int nrays,
-                       int search, int precision, Shape* sh, bool knn_only = false) {
+// Design part: bounding box, centred FP32 copy and its row norms.
+size_t layout_design(const Shape& sh, void* base, Workspace* ws) {
+  Workspace scratch;
+  Workspace* w = ws ? ws : &scratch;   // sizes only when ws is null
+  Carver c{static_cast<char*>(base), 0};
+  w->maxn2 = static_cast<unsigned*>(c.take(4 * sizeof(unsigned)));
+  w->bbox_part = static_cast<double*>(c.take(sizeof(double) * 64 * 2 * sh.p));
+  w->lo = static_cast<double*>(c.take(sizeof(double) * sh.p));
+  w->hi = static_cast<double*>(c.take(sizeof(double) * sh.p));
+  w->center = static_cast<double*>(c.take(sizeof(double) * sh.p));
+  w->Xf = static_cast<float*>(c.take(sizeof(float) * sh.Npad * sh.PP));
+  w->nx = static_cast<float*>(c.take(sizeof(float) * sh.Npad));
+  return c.off;
+}
+
+size_t layout_workspace(const Shape& sh, void* base, Workspace* ws) {
+  Workspace w;
+  std::memset(&w, 0, sizeof(w));
+  const size_t r = layout_request(sh, base, &w);
+  const size_t d = layout_design(sh, base ? static_cast<char*>(base) + r : nullptr, &w);
+  if (ws) *ws = w;
+  return r + d;
+}
+
+bool make_shape(int64_t N, int p, int64_t M, int n0, int n, int N_close, int nrays, int search,
+                int precision, Shape* sh, bool knn_only) {
   if (p < 1 || p > LAGP_MAX_P || N < 1 || M < 0) return false;
   if (n0 < 1 || n0 > n || n > LAGP_MAX_N || n > N_close || N_close > N || N_close > 4096)
     return false;
@@ -97,6 +125,95 @@ extern "C" size_t laGP_workspace_bytes(int64_t N, int p, int64_t M, int n, int N
   return layout_workspace(sh, nullptr, nullptr);
 }
 
+namespace lagp {
+
+// Greedy design + prediction of one chunk whose candidates are in ws.cand.
+static cudaError_t run_design(const DesignArgs& a0, int search, int precision, bool uneven,
+                              cudaStream_t s) {
+  if (precision == LAGP_FP64) return launch_design_fp64(a0, search, s);
+  const Workspace& ws = *a0.ws;
+  DesignArgs a = a0;
+  a.order = nullptr;
+  a.count = nullptr;
+  cudaError_t e;
+  if (search == LAGP_RAY) {
+    if (uneven && a.tune.lpt) {
+      if ((e = launch_order(a, search, 0, 1, s)) != cudaSuccess) return e;
+      a.order = ws.order;
+      a.count = ws.order_count;
+    }
+    return launch_ray32(a, s);
+  }
+  // exhaustive: tensor-core scorer for local designs up to its size limit,
+  // CUDA-core scorer above it (decided per location)
+  const int lim = exh_tc_max_n();
+  if (!uneven) return a.n_max <= lim ? launch_exh_tc(a, s) : launch_exh32(a, s);
+  const int split = a.n_max > lim ? lim : 0;
+  if ((e = launch_order(a, search, split, a.tune.lpt, s)) != cudaSuccess) return e;
+  a.order = ws.order;
+  a.count = ws.order_count;
+  if (split == 0) return launch_exh_tc(a, s);
+  if ((e = launch_exh_tc(a, s)) != cudaSuccess) return e;
+  DesignArgs b = a;
+  b.order = ws.order + ws.chunk;
+  b.count = ws.order_count + 1;
+  return launch_exh32(b, s);
+}
+
+static DesignArgs chunk_args(const Shape& sh, const Call& c, const Workspace& ws, int64_t c0,
+                             int64_t Mc, const Tune& t) {
+  DesignArgs a;
+  const int n = sh.n_max;
+  a.X = c.design; a.Y = c.y; a.N = sh.N; a.p = sh.p; a.PP = sh.PP; a.xref = c.xref + c0 * sh.p;
+  a.M = Mc; a.cand = ws.cand; a.nc_max = sh.nc_max;
+  a.nc_loc = c.nclose_loc ? c.nclose_loc + c0 : nullptr; a.n0 = sh.n0; a.n_max = n;
+  a.n_loc = c.n_loc ? c.n_loc + c0 : nullptr; a.theta = c.theta; a.g = c.g; a.nrays = sh.nrays;
+  a.mean = c.mean + c0; a.s2 = c.s2 + c0;
+  a.selected = c.selected ? c.selected + c0 * n : nullptr;
+  a.tie_gap = c.tie_gap ? c.tie_gap + c0 * n : nullptr;
+  a.nevals = c.nevals ? c.nevals + c0 * n : nullptr;
+  a.ws = &ws; a.order = nullptr; a.count = nullptr; a.tune = t;
+  return a;
+}
+
+// The whole path on the stream: prepare, then per chunk kNN and design.
+int enqueue(const Shape& sh, const Call& c, const Workspace& ws, const Tune& t, cudaStream_t s,
+            bool prepared) {
+  if (cudaMemsetAsync(ws.status, 0, sizeof(unsigned), s) != cudaSuccess) return LAGP_ERR_CUDA;
+  if (!prepared && launch_prepare(c.design, sh.N, sh.p, sh.PP, sh.Npad, ws, s) != cudaSuccess)
+    return LAGP_ERR_CUDA;
+  const bool uneven = c.n_loc || c.nclose_loc;
+  for (int64_t c0 = 0; c0 < sh.M; c0 += sh.chunk) {
+    const int64_t Mc = (sh.M - c0 < sh.chunk) ? sh.M - c0 : sh.chunk;
+    const int32_t* ncl = c.nclose_loc ? c.nclose_loc + c0 : nullptr;
+    if (launch_knn(c.design, sh.N, sh.p, sh.PP, sh.Npad, c.xref + c0 * sh.p, Mc, sh.nc_max, ncl,
+                   ws.cand, ws, s) != cudaSuccess)
+      return LAGP_ERR_CUDA;
+    const DesignArgs a = chunk_args(sh, c, ws, c0, Mc, t);
+    if (run_design(a, sh.search, sh.precision, uneven, s) != cudaSuccess) return LAGP_ERR_CUDA;
+  }
+  return LAGP_OK;
+}
+
+static int check_call(int64_t N, int p, const double* xref, int64_t M, int n0, int n,
+                      int N_close, double theta, double g, int search, int nrays, int precision,
+                      const double* design, const double* y, double* mean, double* s2,
+                      void* workspace, size_t workspace_bytes, Shape* sh, Workspace* ws) {
+  if (!make_shape(N, p, M, n0, n, N_close, nrays, search, precision, sh)) return LAGP_ERR_INVALID;
+  if (!(theta > 0.0) || !(g >= 0.0) || theta != theta) return LAGP_ERR_INVALID;
+  if (M == 0) return 1;
+  if (!design || !y || !xref || !mean || !s2 || !workspace) return LAGP_ERR_INVALID;
+  const size_t need = layout_workspace(*sh, workspace, ws);
+  if (workspace_bytes < need) return LAGP_ERR_WORKSPACE;
+  return LAGP_OK;
+}
+
+Tune tune_for(const Shape& sh, bool uneven) {
+  return lookup_tune(sh.p, sh.n_max, sh.nc_max, sh.nrays, sh.search, uneven ? 1 : 0);
+}
+
+}  // namespace lagp
+
 extern "C" int laGP_build_and_predict(const double* design, const double* y, int64_t N, int p,
                                       const double* xref, int64_t M, int n0, int n, int N_close,
                                       double theta, double g, int search, int nrays,
@@ -105,35 +222,98 @@ extern "C" int laGP_build_and_predict(const double* design, const double* y, int
                                       int32_t* selected, double* tie_gap, int32_t* nevals,
                                       void* workspace, size_t workspace_bytes, void* stream) {
   Shape sh;
-  if (!make_shape(N, p, M, n0, n, N_close, nrays, search, precision, &sh)) return LAGP_ERR_INVALID;
-  if (!(theta > 0.0) || !(g >= 0.0) || theta != theta) return LAGP_ERR_INVALID;
-  if (M == 0) return LAGP_OK;
-  if (!design || !y || !xref || !mean || !s2 || !workspace) return LAGP_ERR_INVALID;
   Workspace ws;
-  const size_t need = layout_workspace(sh, workspace, &ws);
-  if (workspace_bytes < need) return LAGP_ERR_WORKSPACE;
+  const int rc = check_call(N, p, xref, M, n0, n, N_close, theta, g, search, nrays, precision,
+                            design, y, mean, s2, workspace, workspace_bytes, &sh, &ws);
+  if (rc != LAGP_OK) return rc > 0 ? LAGP_OK : rc;
+  const Call c{design, y, xref, theta, g, n_loc, nclose_loc, mean, s2, selected, tie_gap, nevals};
+  return enqueue(sh, c, ws, tune_for(sh, n_loc || nclose_loc), static_cast<cudaStream_t>(stream),
+                 false);
+}
+
+extern "C" int laGP_autotune(const double* design, const double* y, int64_t N, int p,
+                             const double* xref, int64_t M, int n0, int n, int N_close,
+                             double theta, double g, int search, int nrays, int precision,
+                             const int32_t* n_loc, const int32_t* nclose_loc, double* mean,
+                             double* s2, void* workspace, size_t workspace_bytes, void* stream,
+                             int* choice) {
+  Shape sh;
+  Workspace ws;
+  const int rc = check_call(N, p, xref, M, n0, n, N_close, theta, g, search, nrays, precision,
+                            design, y, mean, s2, workspace, workspace_bytes, &sh, &ws);
+  if (rc != LAGP_OK) return rc > 0 ? LAGP_ERR_INVALID : rc;
+  if (!choice) return LAGP_ERR_INVALID;
+  const bool uneven = n_loc || nclose_loc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (cudaMemsetAsync(ws.status, 0, sizeof(unsigned), s) != cudaSuccess) return LAGP_ERR_CUDA;
-  if (launch_prepare(design, N, p, sh.PP, sh.Npad, ws, s) != cudaSuccess) return LAGP_ERR_CUDA;
-  for (int64_t c0 = 0; c0 < M; c0 += sh.chunk) {
-    const int64_t Mc = (M - c0 < sh.chunk) ? M - c0 : sh.chunk;
-    const int32_t* ncl = nclose_loc ? nclose_loc + c0 : nullptr;
-    if (launch_knn(design, N, p, sh.PP, sh.Npad, xref + c0 * p, Mc, N_close, ncl, ws.cand, ws,
-                   s) != cudaSuccess)
-      return LAGP_ERR_CUDA;
-    DesignArgs a;
-    a.X = design; a.Y = y; a.N = N; a.p = p; a.PP = sh.PP; a.xref = xref + c0 * p; a.M = Mc;
-    a.cand = ws.cand; a.nc_max = N_close; a.nc_loc = ncl; a.n0 = n0; a.n_max = n;
-    a.n_loc = n_loc ? n_loc + c0 : nullptr; a.theta = theta; a.g = g; a.nrays = sh.nrays;
-    a.mean = mean + c0; a.s2 = s2 + c0;
-    a.selected = selected ? selected + c0 * n : nullptr;
-    a.tie_gap = tie_gap ? tie_gap + c0 * n : nullptr;
-    a.nevals = nevals ? nevals + c0 * n : nullptr;
-    a.ws = &ws;
-    cudaError_t e = (precision == LAGP_FP64) ? launch_design_fp64(a, search, s)
-                                             : launch_design_fp32(a, search, s);
-    if (e != cudaSuccess) return LAGP_ERR_CUDA;
+  if (precision == LAGP_FP64) {   // the FP64 kernels have no launch choices
+    *choice = encode_tune(default_tune());
+    return LAGP_OK;
   }
+  // candidates: every choice that matters for this shape
+  Tune cand[12];
+  int nc = 0;
+  const int lpts = uneven ? 2 : 1;
+  for (int l = lpts - 1; l >= 0; --l) {
+    if (search == LAGP_RAY) {
+      for (int rw : {2, 1, 4}) cand[nc++] = Tune{rw, l, 1};
+    } else {
+      for (int occ : {1, 2}) cand[nc++] = Tune{2, l, occ};
+    }
+  }
+  // kNN of the first chunk once; then each candidate's design launch, timed
+  const Call c{design, y, xref, theta, g, n_loc, nclose_loc, mean, s2, nullptr, nullptr, nullptr};
+  const int64_t Mc = sh.M < sh.chunk ? sh.M : sh.chunk;
+  if (cudaMemsetAsync(ws.status, 0, sizeof(unsigned), s) != cudaSuccess) return LAGP_ERR_CUDA;
+  if (launch_prepare(design, sh.N, sh.p, sh.PP, sh.Npad, ws, s) != cudaSuccess) return LAGP_ERR_CUDA;
+  if (launch_knn(design, sh.N, sh.p, sh.PP, sh.Npad, xref, Mc, sh.nc_max, nclose_loc, ws.cand, ws,
+                 s) != cudaSuccess)
+    return LAGP_ERR_CUDA;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return LAGP_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return LAGP_ERR_CUDA; }
+  int best = 0;
+  float best_ms = 0.f;
+  int out = LAGP_OK;
+  for (int i = 0; i < nc && out == LAGP_OK; ++i) {
+    const DesignArgs a = chunk_args(sh, c, ws, 0, Mc, cand[i]);
+    float ms = 0.f;
+    if (run_design(a, search, precision, uneven, s) != cudaSuccess ||    // warm-up
+        cudaEventRecord(e0, s) != cudaSuccess ||
+        run_design(a, search, precision, uneven, s) != cudaSuccess ||
+        cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      out = LAGP_ERR_CUDA;
+      break;
+    }
+    if (i == 0 || ms < best_ms) { best = i; best_ms = ms; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (out != LAGP_OK) return out;
+  unsigned st = 0;
+  if (cudaMemcpy(&st, ws.status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return LAGP_ERR_CUDA;
+  if (st) return LAGP_ERR_DEVICE;
+  store_tune(sh.p, sh.n_max, sh.nc_max, sh.nrays, search, uneven ? 1 : 0, cand[best]);
+  *choice = encode_tune(cand[best]);
+  return LAGP_OK;
+}
+
+extern "C" int laGP_tune_get(int p, int n, int N_close, int nrays, int search, int uneven,
+                             int* choice) {
+  if (!choice || p < 1 || p > LAGP_MAX_P) return LAGP_ERR_INVALID;
+  const int R = (search == LAGP_RAY) ? (nrays <= 0 ? p : nrays) : 1;
+  *choice = encode_tune(lookup_tune(p, n, N_close, R, search, uneven ? 1 : 0));
+  return LAGP_OK;
+}
+
+extern "C" int laGP_tune_set(int p, int n, int N_close, int nrays, int search, int uneven,
+                             int choice) {
+  Tune t;
+  if (!decode_tune(choice, &t) || p < 1 || p > LAGP_MAX_P) return LAGP_ERR_INVALID;
+  if (search != LAGP_EXHAUSTIVE && search != LAGP_RAY) return LAGP_ERR_INVALID;
+  const int R = (search == LAGP_RAY) ? (nrays <= 0 ? p : nrays) : 1;
+  store_tune(p, n, N_close, R, search, uneven ? 1 : 0, t);
   return LAGP_OK;
 }
 

@@ -22,11 +22,68 @@ struct Workspace {
   void* knn_buf;        // [chunk][cap] (float d32, int32 index) candidate buffers
   int32_t* knn_cnt;     // [chunk] surviving buffer entries
   int32_t* cand;        // [chunk][nc_max] candidate design indices, nearest first
-  double* state64;      // per-location FP64 state: FP64 form [chunk][nc_max][n_max]
-                        // correlation cache (exhaustive); FP32 form [chunk][n_max][n_ld] L^{-1}
-  float* state32;       // FP32 form, exhaustive: [chunk][n_max][nc_max] correlation cache
+  double* state64;      // FP64 state: FP64 form, exhaustive: [chunk][nc_max][n_max]
+                        // correlation cache; FP32 form: per slot, L^{-1} and its vectors
+  float* state32;       // FP32 form, exhaustive: [slots][n_max][nc_max] correlation cache
+  unsigned* queue;      // [4] work counters of the persistent kernels
+  int32_t* order;       // [2][chunk] work order (largest local designs first), two parts
+  unsigned* order_hist; // [2][256] cost-bucket counts, then offsets
+  unsigned* order_count;// [2] items per part
+  uint16_t* order_key;  // [chunk] part and cost bucket
   int64_t chunk;
 };
+
+// Warp slots of the persistent ray kernel and CTA slots of the persistent
+// exhaustive kernels: their FP64 / correlation scratch is per slot, so a
+// launch holds at most this many locations' state at a time.
+#define RAY_SLOTS 16384
+#define EXH_SLOTS 2048
+int ray32_slots(int64_t chunk);
+int exh_slots(int64_t chunk);
+
+// Launch choices of the FP32-scoring kernels (picked by laGP_autotune, else
+// the defaults).  They schedule work only: no choice changes any result.
+struct Tune {
+  int ray_warps;     // locations (warps) per CTA of the ray kernel: 1, 2 or 4
+  int lpt;           // order uneven work largest-first (1) or by bucket-free scatter (0)
+  int exh_occ;       // exhaustive kernels keep 1/exh_occ of the resident CTAs per SM: 1 or 2
+};
+Tune default_tune();
+Tune lookup_tune(int p, int n_max, int nc_max, int nrays, int search, int uneven);
+void store_tune(int p, int n_max, int nc_max, int nrays, int search, int uneven, const Tune& t);
+int encode_tune(const Tune& t);
+bool decode_tune(int code, Tune* t);
+
+// CTAs of `kernel` that fit on one SM by its registers, threads and shared
+// memory (dynamic `smem` plus static, plus the per-CTA reservation).
+int ctas_per_sm(const void* kernel, int threads, size_t smem);
+
+// Grid of a persistent kernel: CTAs resident at once on the device, at most
+// ceil(items / per_cta) and at most slots / per_cta, so that CTA b's slots
+// b * per_cta .. b * per_cta + per_cta - 1 all exist (returns -1 on a CUDA
+// error or when not even one CTA has its slots).
+// Residency is the larger of the runtime's occupancy figure and the count
+// from the kernel's resources: a grid above residency is still correct (the
+// extra CTAs start late and find less work), one below it idles SMs.
+template <typename K>
+int64_t persistent_grid(K kernel, int threads, size_t smem, int64_t items, int64_t slots,
+                        int per_cta = 1, int occ_div = 1) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess)
+    return -1;
+  const int own = ctas_per_sm(reinterpret_cast<const void*>(kernel), threads, smem);
+  if (own > per_sm) per_sm = own;
+  const int64_t cap = slots / per_cta;
+  if (cap < 1) return -1;
+  int64_t grid = (items + per_cta - 1) / per_cta;
+  int keep = per_sm / (occ_div > 0 ? occ_div : 1);
+  const int64_t resident = (int64_t)sms * (keep > 0 ? keep : 1);
+  if (grid > resident) grid = resident;
+  if (grid > cap) grid = cap;
+  return grid < 1 ? 1 : grid;
+}
 
 struct Shape {
   int64_t N;
@@ -39,8 +96,12 @@ struct Shape {
 };
 
 // Layout of the workspace for a shape; returns total bytes.  With base != null
-// fills ws with pointers into [base, base + bytes).
+// fills ws with pointers into [base, base + bytes).  The workspace is the
+// request part (status word first) followed by the design part; a serving
+// context keeps one design part and gives each request its own request part.
 size_t layout_workspace(const Shape& sh, void* base, Workspace* ws);
+size_t layout_request(const Shape& sh, void* base, Workspace* ws);
+size_t layout_design(const Shape& sh, void* base, Workspace* ws);
 
 int knn_cap(int nc_max);
 size_t knn_smem_stream(int PP);
@@ -72,21 +133,59 @@ struct DesignArgs {
   double* tie_gap;         // [M][n_max] or null
   int32_t* nevals;         // [M][n_max] or null
   const Workspace* ws;
+  const int32_t* order;    // work order of the launch (device) or null
+  const unsigned* count;   // items in `order` (device) or null
+  Tune tune;
 };
 
+// Work order for uneven local designs: counting sort of the chunk's locations
+// by descending cost bucket, split into part 0 (n <= split_n, or all when
+// split_n <= 0) and part 1 (n > split_n).  Fills ws.order and ws.order_count.
+cudaError_t launch_order(const DesignArgs& a, int search, int split_n, int lpt, cudaStream_t s);
+
+// Validated shape of a call (false if an argument is out of range).
+bool make_shape(int64_t N, int p, int64_t M, int n0, int n, int N_close, int nrays, int search,
+                int precision, Shape* sh, bool knn_only = false);
+
+// Arguments of one predictive call (device pointers).
+struct Call {
+  const double* design;
+  const double* y;
+  const double* xref;
+  double theta, g;
+  const int32_t* n_loc;
+  const int32_t* nclose_loc;
+  double* mean;
+  double* s2;
+  int32_t* selected;
+  double* tie_gap;
+  int32_t* nevals;
+};
+
+// Enqueues the whole path for a call on stream s: (design preparation unless
+// `prepared`), then per chunk kNN, greedy design and prediction.  Returns an
+// LAGP_* code.
+int enqueue(const Shape& sh, const Call& c, const Workspace& ws, const Tune& t, cudaStream_t s,
+            bool prepared);
+Tune tune_for(const Shape& sh, bool uneven);
+
 // Opt-in per-kernel timing (CUDA events recorded on the launch stream around
-// each kernel; off unless laGP_profile(1) was called).
+// each kernel; off unless laGP_profile(1) was called).  Suspended while a
+// launch sequence is being captured into a CUDA graph.
 void prof_begin(const char* name, cudaStream_t s);
 void prof_end(cudaStream_t s);
+void prof_suspend(bool on);
 
 cudaError_t launch_design_fp64(const DesignArgs& a, int search, cudaStream_t s);
 // FP32-scoring ray search, one warp per location (ray32.cu); its per-location
 // FP64 scratch in Workspace::state64 holds ray32_g64_doubles(n_max) doubles.
 cudaError_t launch_ray32(const DesignArgs& a, cudaStream_t s);
-// FP32-scoring exhaustive search with tensor-core scoring (exh_tc.cu), n_max <= 64.
-bool exh_tc_supported(int n_max);
+// FP32-scoring exhaustive search with tensor-core scoring (exh_tc.cu) for the
+// locations with n <= exh_tc_max_n().
+int exh_tc_max_n();
 cudaError_t launch_exh_tc(const DesignArgs& a, cudaStream_t s);
 size_t ray32_g64_doubles(int n_max);
-cudaError_t launch_design_fp32(const DesignArgs& a, int search, cudaStream_t s);
+// FP32-scoring exhaustive search with CUDA-core scoring (design_fp32.cu), n_max <= 128.
+cudaError_t launch_exh32(const DesignArgs& a, cudaStream_t s);
 
 }  // namespace lagp

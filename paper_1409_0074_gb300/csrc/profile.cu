@@ -15,6 +15,7 @@ struct Rec {
 };
 std::mutex g_mu;
 bool g_on = false;
+bool g_suspend = false;
 std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_pool;
 
@@ -38,9 +39,14 @@ void recycle_all() {
 }
 }  // namespace
 
+void prof_suspend(bool on) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_suspend = on;
+}
+
 void prof_begin(const char* name, cudaStream_t s) {
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_on) return;
+  if (!g_on || g_suspend) return;
   Rec r{name, take_event(), nullptr};
   if (r.a) cudaEventRecord(r.a, s);
   g_recs.push_back(r);
@@ -48,7 +54,7 @@ void prof_begin(const char* name, cudaStream_t s) {
 
 void prof_end(cudaStream_t s) {
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_on || g_recs.empty() || g_recs.back().b) return;
+  if (!g_on || g_suspend || g_recs.empty() || g_recs.back().b) return;
   g_recs.back().b = take_event();
   if (g_recs.back().b) cudaEventRecord(g_recs.back().b, s);
 }

@@ -16,6 +16,13 @@
 // zeros to a multiple of 4, so every row is read as float4s.
 // The factor itself grows in FP64 (the partitioned update in factored form,
 // Sec 2.2) in global memory, packed lower-triangular.
+//
+// Scheduling.  The kernel is persistent: each warp takes the next location
+// from a device work counter until the queue is empty, optionally through a
+// permutation (largest local designs first, so that uneven n does not leave a
+// long tail).  The FP64 scratch belongs to the warp slot, not the location, so
+// it stays within a few hundred MB (L2-resident for moderate grids) however
+// many locations a launch covers.
 #include <cstdint>
 
 #include "common.cuh"
@@ -23,7 +30,6 @@
 
 namespace lagp {
 
-#define RW_WARPS 2                  // locations per CTA
 #define RAY_MAX_ROUNDS 1100         // bound on evaluation rounds per step
 
 struct RayParams {
@@ -48,9 +54,12 @@ struct RayParams {
   int32_t* selected;
   double* tie_gap;
   int32_t* nevals;
-  double* g64;          // per location: packed L^{-1} (n(n+1)/2) then kx, z, zy, kvec, l (n each)
+  double* g64;          // per warp slot: packed L^{-1} (n(n+1)/2) then kx, z, zy, kvec, l (n each)
   int64_t g64_stride;
   unsigned* status;
+  unsigned* queue;      // work counter (zero at launch)
+  const int32_t* order; // item -> location, or null (identity)
+  const unsigned* count;// number of items (device), or null (M)
 };
 
 // start of row i in the zero-padded FP32 row storage (rows of length
@@ -156,20 +165,17 @@ __device__ __forceinline__ double warp_sum64(double v) {
 
 enum { PH_ALC0 = 0, PH_FIRST = 1, PH_ITER = 2, PH_DONE = 3 };
 
+// One location, by one warp, in the warp's shared-memory region and FP64 slot.
 template <int RP, int PP>
-__global__ void __launch_bounds__(RW_WARPS * 32) ray32_kernel(RayParams P) {
-  extern __shared__ __align__(16) float sm[];
+__device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t loc, float* base,
+                                               double* Lg) {
   constexpr int G = 32 / RP;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t loc = (int64_t)blockIdx.x * RW_WARPS + warp;
-  if (loc >= P.M) return;
-
+  const int lane = threadIdx.x & 31;
   const int p = P.p, ldn = P.n_max, R = P.R;
   const int nc = P.nc_loc ? P.nc_loc[loc] : P.nc_max;
   const int n = P.n_loc ? P.n_loc[loc] : P.n_max;
   const int32_t* cl = P.cand + loc * P.nc_max;
   const WarpLayout lay = warp_layout(ldn, PP, RP, P.nc_max);
-  float* base = sm + (size_t)warp * (lay.bytes / 4);
   float* Lf = base + lay.lf;
   float* kzb = base + lay.kz;
   float* zf = base + lay.zf;
@@ -186,7 +192,6 @@ __global__ void __launch_bounds__(RW_WARPS * 32) ray32_kernel(RayParams P) {
   uint32_t* smask = reinterpret_cast<uint32_t*>(base + lay.smask);   // this step's ray starts
   const int KP = kz_ld(ldn);
 
-  double* Lg = P.g64 + loc * P.g64_stride;
   double* kx64 = Lg + tri(ldn);
   double* z64 = kx64 + ldn;
   double* zy64 = z64 + ldn;
@@ -506,7 +511,46 @@ __global__ void __launch_bounds__(RW_WARPS * 32) ray32_kernel(RayParams P) {
     for (int i = lane; i < ldn; i += 32) P.selected[loc * ldn + i] = (i < j) ? cl[sel[i]] : -1;
 }
 
+template <int RP, int PP, int RW>
+__global__ void __launch_bounds__(RW * 32) ray32_kernel(RayParams P) {
+  extern __shared__ __align__(16) float sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const WarpLayout lay = warp_layout(P.n_max, PP, RP, P.nc_max);
+  float* base = sm + (size_t)warp * (lay.bytes / 4);
+  double* Lg = P.g64 + ((int64_t)blockIdx.x * RW + warp) * P.g64_stride;
+  const unsigned items = P.count ? *P.count : (unsigned)P.M;
+  for (;;) {
+    unsigned it = 0;
+    if (lane == 0) it = atomicAdd(P.queue, 1u);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= items) break;
+    ray32_location<RP, PP>(P, P.order ? (int64_t)P.order[it] : (int64_t)it, base, Lg);
+    __syncwarp();
+  }
+}
+
 size_t ray32_g64_doubles(int n_max) { return (size_t)tri(n_max) + 5 * (size_t)n_max; }
+
+// Warp slots for a chunk: at least one CTA of the widest choice (4 warps) and a
+// multiple of 4, so that every warp of every launched CTA owns a slot.
+int ray32_slots(int64_t chunk) {
+  const int64_t s = chunk < RAY_SLOTS ? chunk : RAY_SLOTS;
+  return (int)((s + 3) / 4 * 4);
+}
+
+template <int RP, int PP, int RW>
+static cudaError_t ray32_go(const RayParams& P, size_t sm, int slots, cudaStream_t s) {
+  auto k = ray32_kernel<RP, PP, RW>;
+  cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (err != cudaSuccess) return err;
+  const int64_t grid = persistent_grid(k, RW * 32, sm, P.M, slots, RW);
+  if (grid < 0) return cudaErrorInvalidValue;
+  if ((err = cudaMemsetAsync(P.queue, 0, sizeof(unsigned), s)) != cudaSuccess) return err;
+  prof_begin("ray32", s);
+  k<<<(unsigned)grid, RW * 32, sm, s>>>(P);
+  prof_end(s);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_ray32(const DesignArgs& a, cudaStream_t s) {
   RayParams P;
@@ -516,32 +560,28 @@ cudaError_t launch_ray32(const DesignArgs& a, cudaStream_t s) {
   P.hi = a.ws->hi; P.center = a.ws->center; P.mean = a.mean; P.s2 = a.s2;
   P.selected = a.selected; P.tie_gap = a.tie_gap; P.nevals = a.nevals; P.g64 = a.ws->state64;
   P.g64_stride = (int64_t)ray32_g64_doubles(a.n_max); P.status = a.ws->status;
+  P.queue = a.ws->queue; P.order = a.order; P.count = a.count;
   int RP = 2;
   while (RP < a.nrays) RP <<= 1;
   const WarpLayout lay = warp_layout(a.n_max, a.PP, RP, a.nc_max);
-  const size_t sm = (size_t)lay.bytes * RW_WARPS;
-  const unsigned grid = (unsigned)((a.M + RW_WARPS - 1) / RW_WARPS);
-  cudaError_t err = cudaSuccess;
-  const int key = RP * 100 + a.PP;
+  const int RW = a.tune.ray_warps;
+  const size_t sm = (size_t)lay.bytes * RW;
+  const int slots = ray32_slots(a.ws->chunk);
+  const int key = (RW * 100 + RP) * 100 + a.PP;
   switch (key) {
-#define RAY_CASE(RPV, PPV)                                                                   \
-  case RPV * 100 + PPV:                                                                      \
-    err = cudaFuncSetAttribute(ray32_kernel<RPV, PPV>,                                       \
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);        \
-    if (err != cudaSuccess) return err;                                                      \
-    prof_begin("ray32", s);                                                                  \
-    ray32_kernel<RPV, PPV><<<grid, RW_WARPS * 32, sm, s>>>(P);                               \
-    prof_end(s);                                                                             \
-    break;
-    RAY_CASE(2, 4) RAY_CASE(2, 8) RAY_CASE(2, 12) RAY_CASE(2, 16)
-    RAY_CASE(4, 4) RAY_CASE(4, 8) RAY_CASE(4, 12) RAY_CASE(4, 16)
-    RAY_CASE(8, 4) RAY_CASE(8, 8) RAY_CASE(8, 12) RAY_CASE(8, 16)
-    RAY_CASE(16, 4) RAY_CASE(16, 8) RAY_CASE(16, 12) RAY_CASE(16, 16)
+#define RAY_CASE(RWV, RPV, PPV) \
+  case (RWV * 100 + RPV) * 100 + PPV: return ray32_go<RPV, PPV, RWV>(P, sm, slots, s);
+#define RAY_CASES(RWV)                                                                   \
+    RAY_CASE(RWV, 2, 4) RAY_CASE(RWV, 2, 8) RAY_CASE(RWV, 2, 12) RAY_CASE(RWV, 2, 16)     \
+    RAY_CASE(RWV, 4, 4) RAY_CASE(RWV, 4, 8) RAY_CASE(RWV, 4, 12) RAY_CASE(RWV, 4, 16)     \
+    RAY_CASE(RWV, 8, 4) RAY_CASE(RWV, 8, 8) RAY_CASE(RWV, 8, 12) RAY_CASE(RWV, 8, 16)     \
+    RAY_CASE(RWV, 16, 4) RAY_CASE(RWV, 16, 8) RAY_CASE(RWV, 16, 12) RAY_CASE(RWV, 16, 16)
+    RAY_CASES(1) RAY_CASES(2) RAY_CASES(4)
+#undef RAY_CASES
 #undef RAY_CASE
     default:
       return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 }  // namespace lagp

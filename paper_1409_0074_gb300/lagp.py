@@ -21,9 +21,15 @@ ERRORS = {-1: "invalid argument", -2: "workspace too small", -3: "CUDA error",
           -4: "device reported a failure"}
 STATUS_BITS = {1: "timeout", 2: "kNN tie capacity", 4: "numeric (v <= 0)"}
 
+LAGP_BUSY = 1
+
 EXPORTED = ("laGP_workspace_bytes", "laGP_build_and_predict", "laGP_knn_workspace_bytes",
             "laGP_knn", "laGP_status", "laGP_host_workspace_bytes",
-            "laGP_build_and_predict_host", "laGP_profile", "laGP_profile_read")
+            "laGP_build_and_predict_host", "laGP_profile", "laGP_profile_read",
+            "laGP_autotune", "laGP_tune_get", "laGP_tune_set", "laGP_plan_create",
+            "laGP_plan_launch", "laGP_plan_destroy", "laGP_ctx_design_bytes",
+            "laGP_ctx_request_bytes", "laGP_ctx_create", "laGP_ctx_submit", "laGP_ctx_poll",
+            "laGP_ctx_wait", "laGP_ctx_capacity", "laGP_ctx_destroy")
 
 _lib = None
 
@@ -67,6 +73,37 @@ def load():
     lib.laGP_profile_read.restype = i32
     lib.laGP_profile_read.argtypes = [i32, C.c_char_p, C.POINTER(C.c_double),
                                       C.POINTER(C.c_int32)]
+    ip = C.POINTER(C.c_int)
+    lib.laGP_autotune.restype = i32
+    lib.laGP_autotune.argtypes = [vp, vp, i64, i32, vp, i64, i32, i32, i32, dbl, dbl, i32, i32,
+                                  i32, vp, vp, vp, vp, vp, sz, vp, ip]
+    lib.laGP_tune_get.restype = i32
+    lib.laGP_tune_get.argtypes = [i32, i32, i32, i32, i32, i32, ip]
+    lib.laGP_tune_set.restype = i32
+    lib.laGP_tune_set.argtypes = [i32, i32, i32, i32, i32, i32, i32]
+    lib.laGP_plan_create.restype = i32
+    lib.laGP_plan_create.argtypes = full[:-1] + [C.POINTER(vp)]
+    lib.laGP_plan_launch.restype = i32
+    lib.laGP_plan_launch.argtypes = [vp, vp]
+    lib.laGP_plan_destroy.restype = i32
+    lib.laGP_plan_destroy.argtypes = [vp]
+    lib.laGP_ctx_design_bytes.restype = sz
+    lib.laGP_ctx_design_bytes.argtypes = [i64, i32]
+    lib.laGP_ctx_request_bytes.restype = sz
+    lib.laGP_ctx_request_bytes.argtypes = [i64, i32, i64, i32, i32, i32, i32, i32, i32]
+    lib.laGP_ctx_create.restype = i32
+    lib.laGP_ctx_create.argtypes = [vp, vp, i64, i32, dbl, dbl, i32, i32, i32, i32, i32, vp, sz,
+                                    i32, C.POINTER(vp)]
+    lib.laGP_ctx_submit.restype = i32
+    lib.laGP_ctx_submit.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp, C.POINTER(C.c_int64)]
+    lib.laGP_ctx_poll.restype = i32
+    lib.laGP_ctx_poll.argtypes = [vp, C.c_int64, ip]
+    lib.laGP_ctx_wait.restype = i32
+    lib.laGP_ctx_wait.argtypes = [vp, C.c_int64]
+    lib.laGP_ctx_capacity.restype = i32
+    lib.laGP_ctx_capacity.argtypes = [vp, C.POINTER(C.c_size_t), ip]
+    lib.laGP_ctx_destroy.restype = i32
+    lib.laGP_ctx_destroy.argtypes = [vp]
     _lib = lib
     return lib
 
@@ -217,3 +254,145 @@ def predict(design, y, xref, n0, n, N_close, theta, g, search="ray", nrays=0, pr
     if rc != 0:
         raise LagpError("laGP_build_and_predict (device)", rc, st)
     return out
+
+
+def _args_common(design, y, xref, n0, n, N_close, theta, g, search, nrays, precision, n_loc,
+                 nclose_loc):
+    import torch
+    N, p = design.shape
+    M = xref.shape[0]
+    return [_ptr(design, torch.float64), _ptr(y, torch.float64, N), N, p,
+            _ptr(xref, torch.float64), M, n0, n, N_close, float(theta), float(g), search, nrays,
+            precision, _ptr(n_loc, torch.int32, M), _ptr(nclose_loc, torch.int32, M)]
+
+
+def laGP_autotune(design, y, xref, n0, n, N_close, theta, g, search, nrays, precision, mean, s2,
+                  workspace, n_loc=None, nclose_loc=None, stream=None):
+    """Times the launch choices on these locations; returns the stored choice code."""
+    import torch
+    M = xref.shape[0]
+    choice = C.c_int(0)
+    rc = load().laGP_autotune(*_args_common(design, y, xref, n0, n, N_close, theta, g, search,
+                                            nrays, precision, n_loc, nclose_loc),
+                              _ptr(mean, torch.float64, M), _ptr(s2, torch.float64, M),
+                              _ptr(workspace), workspace.numel() * workspace.element_size(),
+                              _stream(stream), C.byref(choice))
+    _check("laGP_autotune", rc)
+    return choice.value
+
+
+def laGP_tune_get(p, n, N_close, nrays, search, uneven):
+    choice = C.c_int(0)
+    _check("laGP_tune_get", load().laGP_tune_get(p, n, N_close, nrays, search, int(uneven),
+                                                 C.byref(choice)))
+    return choice.value
+
+
+def laGP_tune_set(p, n, N_close, nrays, search, uneven, choice):
+    _check("laGP_tune_set", load().laGP_tune_set(p, n, N_close, nrays, search, int(uneven),
+                                                 int(choice)))
+
+
+class Plan:
+    """A captured launch sequence (laGP_plan_create); keeps references to its
+    tensors so that they outlive the plan."""
+
+    def __init__(self, design, y, xref, n0, n, N_close, theta, g, search, nrays, precision, mean,
+                 s2, workspace, n_loc=None, nclose_loc=None, selected=None, tie_gap=None,
+                 nevals=None):
+        import torch
+        M = xref.shape[0]
+        self._keep = (design, y, xref, mean, s2, workspace, n_loc, nclose_loc, selected, tie_gap,
+                      nevals)
+        h = C.c_void_p(0)
+        rc = load().laGP_plan_create(
+            *_args_common(design, y, xref, n0, n, N_close, theta, g, search, nrays, precision,
+                          n_loc, nclose_loc),
+            _ptr(mean, torch.float64, M), _ptr(s2, torch.float64, M),
+            _ptr(selected, torch.int32, M * n), _ptr(tie_gap, torch.float64, M * n),
+            _ptr(nevals, torch.int32, M * n), _ptr(workspace),
+            workspace.numel() * workspace.element_size(), C.byref(h))
+        _check("laGP_plan_create", rc)
+        self._h = h
+
+    def launch(self, stream=None):
+        _check("laGP_plan_launch", load().laGP_plan_launch(self._h, _stream(stream)))
+
+    def close(self):
+        if self._h:
+            load().laGP_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Context:
+    """Serving context (laGP_ctx_*): device-resident design in a torch-allocated
+    arena, requests admitted into in-flight slots by free arena space."""
+
+    def __init__(self, design, y, theta, g, n0, N_close, search, nrays, precision, arena_bytes,
+                 max_inflight=8):
+        import torch
+        N, p = design.shape
+        self.N, self.p, self.N_close, self.nrays = N, p, N_close, nrays
+        self.search, self.precision = search, precision
+        self._arena = torch.empty(arena_bytes, dtype=torch.uint8, device=design.device)
+        self._keep = (design, y)
+        h = C.c_void_p(0)
+        rc = load().laGP_ctx_create(_ptr(design, torch.float64), _ptr(y, torch.float64, N), N, p,
+                                    float(theta), float(g), n0, N_close, search, nrays, precision,
+                                    _ptr(self._arena), arena_bytes, max_inflight, C.byref(h))
+        _check("laGP_ctx_create", rc)
+        self._h = h
+
+    def request_bytes(self, M, n, want_selected=False):
+        return load().laGP_ctx_request_bytes(self.N, self.p, M, n, self.N_close, self.nrays,
+                                             self.search, self.precision, int(want_selected))
+
+    def submit(self, xref, n, mean, s2, n_loc=None, selected=None):
+        """xref [M][p] float64, n_loc [M] int32 or None, outputs: numpy arrays
+        (page-locked for asynchronous copies).  Returns a ticket, or None when
+        the context is busy (LAGP_BUSY)."""
+        M = xref.shape[0]
+        t = C.c_int64(0)
+        rc = load().laGP_ctx_submit(self._h, _hptr(xref, np.float64, M * self.p), M, n,
+                                    _hptr(n_loc, np.int32, M), _hptr(mean, np.float64, M),
+                                    _hptr(s2, np.float64, M), _hptr(selected, np.int32, M * n),
+                                    C.byref(t))
+        if rc == LAGP_BUSY:
+            return None
+        _check("laGP_ctx_submit", rc)
+        return t.value
+
+    def poll(self, ticket):
+        """True once the request's outputs are in its host arrays (raises on a
+        device-reported failure)."""
+        done = C.c_int(0)
+        rc = load().laGP_ctx_poll(self._h, ticket, C.byref(done))
+        _check("laGP_ctx_poll", rc)
+        return bool(done.value)
+
+    def wait(self, ticket):
+        _check("laGP_ctx_wait", load().laGP_ctx_wait(self._h, ticket))
+
+    def capacity(self):
+        free = C.c_size_t(0)
+        slots = C.c_int(0)
+        _check("laGP_ctx_capacity", load().laGP_ctx_capacity(self._h, C.byref(free),
+                                                             C.byref(slots)))
+        return free.value, slots.value
+
+    def close(self):
+        if self._h:
+            load().laGP_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

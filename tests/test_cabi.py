@@ -83,3 +83,41 @@ def test_invalid_calls_return_before_touching_the_device(lib):
     # M == 0 is a no-op
     assert f(fake, fake, 1000, 2, fake, 0, 3, 10, 100, 0.1, 1e-6, 0, 2, 0, None, None, fake, fake,
              None, None, None, fake, 1 << 30, None) == 0
+
+
+def test_host_only_entry_points_of_tuning_plans_and_contexts(lib):
+    """Sizes, the launch-choice table and argument checks of the plan and
+    serving-context entry points need no device."""
+    from paper_1409_0074_gb300 import lagp
+    vp = C.c_void_p
+    d = lib.laGP_ctx_design_bytes(1_000_000, 8)
+    assert d >= 1_000_000 * 8 * 4          # at least the FP32 design copy
+    r1 = lib.laGP_ctx_request_bytes(1_000_000, 8, 500, 50, 1000, 8, 1, 1, 0)
+    r2 = lib.laGP_ctx_request_bytes(1_000_000, 8, 1000, 50, 1000, 8, 1, 1, 0)
+    r3 = lib.laGP_ctx_request_bytes(1_000_000, 8, 500, 50, 1000, 8, 1, 1, 1)
+    assert 0 < r1 < r2 and r3 > r1
+    assert lib.laGP_ctx_request_bytes(1_000_000, 8, 0, 50, 1000, 8, 1, 1, 0) == 0
+    # launch-choice table: defaults, set, get, invalid codes
+    assert lagp.laGP_tune_get(3, 40, 500, 3, 1, 0) == 2 | 16
+    lagp.laGP_tune_set(3, 40, 500, 3, 1, 0, 4 | 32)
+    assert lagp.laGP_tune_get(3, 40, 500, 3, 1, 0) == 4 | 32
+    assert lagp.laGP_tune_get(3, 40, 500, 3, 1, 1) == 2 | 16        # other key untouched
+    for bad in (0, 3, 5, 2 | 64):
+        assert lib.laGP_tune_set(3, 40, 500, 3, 1, 0, bad) == -1
+    # plans and contexts reject invalid arguments before touching a device
+    h = vp(0)
+    assert lib.laGP_plan_create(None, None, 1000, 2, None, 10, 3, 10, 100, 0.1, 1e-6, 1, 2, 1,
+                                None, None, None, None, None, None, None, None, 0,
+                                C.byref(h)) == -1
+    assert lib.laGP_ctx_create(None, None, 1000, 2, 0.1, 1e-6, 6, 100, 1, 2, 1, None, 0, 4,
+                               C.byref(h)) == -1
+    fake = 4096
+    assert lib.laGP_ctx_create(fake, fake, 1000, 2, 0.1, 1e-6, 6, 100, 1, 2, 1, fake, 1 << 30,
+                               0, C.byref(h)) == -1                 # no slots
+    assert lib.laGP_ctx_create(fake, fake, 1000, 2, 0.1, 1e-6, 6, 100, 1, 2, 1, fake + 8,
+                               1 << 30, 4, C.byref(h)) == -1        # misaligned arena
+    assert lib.laGP_ctx_create(fake, fake, 1000, 2, 0.1, 1e-6, 6, 100, 1, 2, 1, fake, 64, 4,
+                               C.byref(h)) == -2                    # arena below the design part
+    done = C.c_int(0)
+    assert lib.laGP_ctx_poll(None, 1, C.byref(done)) == -1
+    assert lib.laGP_plan_launch(None, None) == -1

@@ -1,0 +1,179 @@
+"""Batching form (uneven n and N' per location, persistent kernels, largest-
+first work order, launch choices, autotuner, captured CUDA-graph plans),
+through the C ABI.
+
+Launch choices schedule work only, so every choice must give bit-identical
+results; a captured plan must reproduce the direct call bit for bit, also
+after its input buffer is refilled in place.  The uneven FP32-scoring form is
+checked against the oracle like the uniform one.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import check_fp32_form, to_dev
+from paper_1409_0074_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lagp(cuda):
+    from paper_1409_0074_gb300 import build
+    build.build()
+    from paper_1409_0074_gb300 import lagp as L
+    L.load()
+    return L
+
+
+@pytest.fixture(scope="module")
+def uneven():
+    return W.uneven_8d(M=4000)
+
+
+def _run(L, w, search, M=None, **kw):
+    import torch
+    M = M or w.M
+    out = L.predict(to_dev(w.X), to_dev(w.Y), to_dev(w.Xref[:M]), w.n0, int(w.n_arr.max()),
+                    int(w.nc_arr.max()), w.theta, w.g, search=search, nrays=8, precision="fp32",
+                    n_loc=to_dev(w.n_arr[:M], torch.int32),
+                    nclose_loc=to_dev(w.nc_arr[:M], torch.int32), want_trace=True, **kw)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def _same(a, b):
+    for k in ("mean", "s2", "selected"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+
+
+@pytest.mark.parametrize("search", ["ray", "exhaustive"])
+def test_launch_choices_do_not_change_results(lagp, uneven, search):
+    n, nc = int(uneven.n_arr.max()), int(uneven.nc_arr.max())
+    s = lagp.SEARCH[search]
+    M = 1500 if search == "ray" else 600
+    before = lagp.laGP_tune_get(8, n, nc, 8, s, 1)
+    try:
+        ref = None
+        codes = [1 | 16, 2 | 16, 4 | 16, 2, 2 | 16 | 32]
+        for code in codes:
+            lagp.laGP_tune_set(8, n, nc, 8, s, 1, code)
+            assert lagp.laGP_tune_get(8, n, nc, 8, s, 1) == code
+            got = _run(lagp, uneven, search, M)
+            if ref is None:
+                ref = got
+            else:
+                _same(ref, got)
+    finally:
+        lagp.laGP_tune_set(8, n, nc, 8, s, 1, before)
+
+
+def test_autotune_stores_a_choice_and_keeps_results(lagp, uneven):
+    import torch
+    w = uneven
+    M = 1200
+    n, nc = int(w.n_arr.max()), int(w.nc_arr.max())
+    ref = _run(lagp, w, "ray", M)
+    X, Y, Xr = to_dev(w.X), to_dev(w.Y), to_dev(w.Xref[:M])
+    nl, ncl = to_dev(w.n_arr[:M], torch.int32), to_dev(w.nc_arr[:M], torch.int32)
+    wsb = lagp.laGP_workspace_bytes(w.N, w.p, M, n, nc, 8, lagp.LAGP_RAY, lagp.LAGP_FP32_SCORE)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    mean = torch.empty(M, dtype=torch.float64, device="cuda")
+    s2 = torch.empty(M, dtype=torch.float64, device="cuda")
+    code = lagp.laGP_autotune(X, Y, Xr, w.n0, n, nc, w.theta, w.g, lagp.LAGP_RAY, 8,
+                              lagp.LAGP_FP32_SCORE, mean, s2, ws, n_loc=nl, nclose_loc=ncl)
+    assert code & 15 in (1, 2, 4) and code & ~63 == 0
+    assert lagp.laGP_tune_get(8, n, nc, 8, lagp.LAGP_RAY, 1) == code
+    _same(ref, _run(lagp, w, "ray", M))
+
+
+@pytest.mark.parametrize("search", ["ray", "exhaustive"])
+def test_uneven_fp32_form_vs_oracle(lagp, uneven, search):
+    """Per-location n ~ U{20..100}, N' ~ U{300..2000}: sampled locations against
+    the oracle run with the same per-location sizes."""
+    M = 160 if search == "ray" else 96
+    g = _run(lagp, uneven, search, M)
+    o = oracle.predict(uneven.X, uneven.Y, uneven.Xref[:M], uneven.n0, int(uneven.n_arr.max()),
+                       int(uneven.nc_arr.max()), uneven.theta, uneven.g, search, nrays=8,
+                       n_arr=uneven.n_arr[:M], nc_arr=uneven.nc_arr[:M], nthreads=0)
+    s = W.Workload(**{k: getattr(uneven, k) for k in ("name", "N", "p", "M", "n0", "n", "nc",
+                                                       "theta", "g", "search", "nrays",
+                                                       "response")})
+    s.X, s.Y, s.Xref, s.Ytrue, s.M = uneven.X, uneven.Y, uneven.Xref[:M], uneven.Ytrue[:M], M
+    # each location's design has exactly its own n points
+    assert np.array_equal((g["selected"] >= 0).sum(axis=1), uneven.n_arr[:M])
+    check_fp32_form(s, g, o, rmse_tol=0.05, max_gap=1e-3 if search == "ray" else None)
+
+
+@pytest.mark.parametrize("search,uneven_sizes", [("ray", False), ("exhaustive", True)])
+def test_plan_replays_match_direct_calls(lagp, uneven, search, uneven_sizes):
+    import torch
+    w = uneven
+    M = 800
+    n, nc = int(w.n_arr.max()), int(w.nc_arr.max())
+    if not uneven_sizes:
+        n, nc = 50, 1000
+    s = lagp.SEARCH[search]
+    X, Y = to_dev(w.X), to_dev(w.Y)
+    xa, xb = to_dev(w.Xref[:M]), to_dev(w.Xref[M:2 * M])
+    kw = {}
+    if uneven_sizes:
+        kw = dict(n_loc=to_dev(w.n_arr[:M], torch.int32),
+                  nclose_loc=to_dev(w.nc_arr[:M], torch.int32))
+    direct_a = lagp.predict(X, Y, xa, w.n0, n, nc, w.theta, w.g, search=search, nrays=8,
+                            precision="fp32", **kw)
+    direct_b = lagp.predict(X, Y, xb, w.n0, n, nc, w.theta, w.g, search=search, nrays=8,
+                            precision="fp32", **kw)
+    wsb = lagp.laGP_workspace_bytes(w.N, w.p, M, n, nc, 8, s, lagp.LAGP_FP32_SCORE)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    xin = xa.clone()
+    mean = torch.full((M,), -1.0, dtype=torch.float64, device="cuda")
+    s2 = torch.full((M,), -1.0, dtype=torch.float64, device="cuda")
+    plan = lagp.Plan(X, Y, xin, w.n0, n, nc, w.theta, w.g, s, 8, lagp.LAGP_FP32_SCORE, mean, s2,
+                     ws, **kw)
+    torch.cuda.synchronize()
+    assert (mean == -1.0).all()                       # capture runs nothing
+    for _ in range(2):
+        plan.launch()
+        torch.cuda.synchronize()
+        assert lagp.laGP_status(ws)[0] == 0
+        assert torch.equal(mean, direct_a["mean"]) and torch.equal(s2, direct_a["s2"])
+    xin.copy_(xb)                                      # new locations, same buffer
+    plan.launch()
+    torch.cuda.synchronize()
+    assert torch.equal(mean, direct_b["mean"]) and torch.equal(s2, direct_b["s2"])
+    plan.close()
+
+
+@pytest.mark.parametrize("search", ["ray", "exhaustive"])
+def test_tiny_batches_match_a_large_batch(lagp, uneven, search):
+    """Calls with fewer locations than a CTA has warps: every warp still owns
+    scratch; each location's result equals the same location's in a larger
+    call."""
+    n, nc = int(uneven.n_arr.max()), int(uneven.nc_arr.max())
+    s = lagp.SEARCH[search]
+    big = _run(lagp, uneven, search, 64)
+    before = lagp.laGP_tune_get(8, n, nc, 8, s, 1)
+    try:
+        for code in ((1 | 16, 2 | 16, 4 | 16) if search == "ray" else (2 | 16,)):
+            lagp.laGP_tune_set(8, n, nc, 8, s, 1, code)
+            for M in (1, 2, 3, 5):
+                small = _run(lagp, uneven, search, M)
+                for k in ("mean", "s2", "selected"):
+                    np.testing.assert_array_equal(small[k], big[k][:M], err_msg=(code, M, k))
+    finally:
+        lagp.laGP_tune_set(8, n, nc, 8, s, 1, before)
+
+
+def test_single_location_uniform_ray(lagp, uneven):
+    import torch
+    w = uneven
+    X, Y = to_dev(w.X), to_dev(w.Y)
+    big = lagp.predict(X, Y, to_dev(w.Xref[:8]), w.n0, 50, 1000, w.theta, w.g, search="ray",
+                       nrays=8, precision="fp32")
+    for m in range(3):
+        one = lagp.predict(X, Y, to_dev(w.Xref[m:m + 1]), w.n0, 50, 1000, w.theta, w.g,
+                           search="ray", nrays=8, precision="fp32")
+        torch.cuda.synchronize()
+        assert torch.equal(one["mean"], big["mean"][m:m + 1])
+        assert torch.equal(one["s2"], big["s2"][m:m + 1])
