@@ -54,14 +54,19 @@ def parse():
     return ap.parse_args()
 
 
-def dist_init(args):
+def dist_init(args, backend="nccl"):
+    """One process per GPU (torchrun's environment).  Locations are
+    independent, so ranks share no data: each predicts its own batch (weak
+    scaling); the process group carries only a barrier and the max-reduce of
+    the timed region."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-        dist.init_process_group("nccl")
+        if backend == "nccl":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group(backend)
     return rank, world
 
 
@@ -76,9 +81,17 @@ def max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(units_per_rank, steps, ms, world):
+    """Units per second of the whole job: all ranks' units over the slowest
+    rank's time.  Returns (rate, slowest ms)."""
+    ms_max = max_over_ranks(ms, world)
+    return world * units_per_rank * steps / (ms_max / 1e3), ms_max
 
 
 class Clocks:
@@ -195,12 +208,11 @@ def run_ours(args, rank, world):
     lagp.laGP_profile(False)
     barrier(world)
     ms = e0.elapsed_time(e1)
-    ms_max = max_over_ranks(ms, world)
+    value, ms_max = whole_job_rate(M, args.steps, ms, world)
     prof = lagp.laGP_profile_read()
     rc, st = lagp.laGP_status(ws)
     if rc != 0:
         raise RuntimeError("device status %d in the timed region" % st)
-    value = world * M * args.steps / (ms_max / 1e3)
 
     # dominant kernel and its roofline
     top = max(prof.items(), key=lambda kv: kv[1][0])
