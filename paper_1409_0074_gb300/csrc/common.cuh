@@ -80,6 +80,68 @@ __device__ __forceinline__ double corr64(const double* a, const double* b, int p
   return exp_cw(-(__ddiv_rn(sqdist64(a, b, p), theta)));
 }
 
+// exp(x) in binary64 for x <= 0 by the same method as exp_cw (Cody-Waite
+// reduction, degree-13 Taylor polynomial on |r| <= ln2/2, scaling by 2^k),
+// evaluated with fused multiply-adds: a few ulp, and about half the FP64
+// instructions of exp_cw.  Results below the normal range are 0.
+__device__ __forceinline__ double exp_neg_fma(double x) {
+  if (x < -708.0) return 0.0;
+  const double inv_ln2 = 0x1.71547652b82fep+0;
+  const double ln2_hi = 0x1.62e42fee00000p-1;
+  const double ln2_lo = 0x1.a39ef35793c76p-33;
+  const double kd = rint(x * inv_ln2);
+  double r = fma(-kd, ln2_hi, x);
+  r = fma(-kd, ln2_lo, r);
+  double s = 1.0 / 6227020800.0;
+  s = fma(s, r, 1.0 / 479001600.0);
+  s = fma(s, r, 1.0 / 39916800.0);
+  s = fma(s, r, 1.0 / 3628800.0);
+  s = fma(s, r, 1.0 / 362880.0);
+  s = fma(s, r, 1.0 / 40320.0);
+  s = fma(s, r, 1.0 / 5040.0);
+  s = fma(s, r, 1.0 / 720.0);
+  s = fma(s, r, 1.0 / 120.0);
+  s = fma(s, r, 1.0 / 24.0);
+  s = fma(s, r, 1.0 / 6.0);
+  s = fma(s, r, 0.5);
+  s = fma(s, r, 1.0);
+  s = fma(s, r, 1.0);
+  // 2^k with k in [-1022, 0]: add k to the exponent field of s (s in [0.7, 1.5])
+  return __longlong_as_double(__double_as_longlong(s) + (long long)(int)kd * (1ll << 52));
+}
+
+// Correlation in binary64 for the FP32-scoring form's factor update: the same
+// quantity as corr64, with FMA contraction and a multiply by -1/theta instead
+// of the division (no bit-exactness with the oracle is needed there, only
+// binary64 accuracy).
+__device__ __forceinline__ double corr64_fast(const double* a, const double* b, int p,
+                                              double neg_inv_theta) {
+  double d0 = 0.0, d1 = 0.0;
+  int k = 0;
+  for (; k + 1 < p; k += 2) {
+    const double t0 = a[k] - b[k], t1 = a[k + 1] - b[k + 1];
+    d0 = fma(t0, t0, d0);
+    d1 = fma(t1, t1, d1);
+  }
+  if (k < p) { const double t = a[k] - b[k]; d0 = fma(t, t, d0); }
+  return exp_neg_fma((d0 + d1) * neg_inv_theta);
+}
+
+// sum_{k=0..len-1} u[k] * v[k] in binary64 with four independent accumulators
+// (GB300's FP64 latency makes a single FMA chain the critical path).
+__device__ __forceinline__ double dot64_ilp(const double* u, const double* v, int len) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int k = 0;
+  for (; k + 3 < len; k += 4) {
+    a0 = fma(u[k], v[k], a0);
+    a1 = fma(u[k + 1], v[k + 1], a1);
+    a2 = fma(u[k + 2], v[k + 2], a2);
+    a3 = fma(u[k + 3], v[k + 3], a3);
+  }
+  for (; k < len; ++k) a0 = fma(u[k], v[k], a0);
+  return (a0 + a1) + (a2 + a3);
+}
+
 __device__ __forceinline__ double relgap64(double a, double b) {
   double m = fmax(fabs(a), fabs(b));
   if (m == 0.0) return 0.0;

@@ -159,13 +159,13 @@ __device__ bool add_point32(const D32Params& P, L32& L, const int32_t* cl, int n
   if (tid < p) L.S64[j * p + tid] = c[tid];
   if (tid < P.PP) L.Sf[j * P.PP + tid] = cand_f(P, cl, r)[tid];
   __syncthreads();
-  for (int i = tid; i < j; i += blockDim.x) L.kvec[i] = corr64(L.S64 + i * p, L.S64 + j * p, p, P.theta);
+  const double nit64 = -1.0 / P.theta;
+  for (int i = tid; i < j; i += blockDim.x)
+    L.kvec[i] = corr64_fast(L.S64 + i * p, L.S64 + j * p, p, nit64);
   __syncthreads();
   double vv = 0.0, dummy = 0.0;
   for (int i = tid; i < j; i += blockDim.x) {
-    const double* Li = Lg + (int64_t)i * ld;
-    double acc = 0.0;
-    for (int k = 0; k <= i; ++k) acc = fma(Li[k], L.kvec[k], acc);
+    const double acc = dot64_ilp(Lg + (int64_t)i * ld, L.kvec, i + 1);
     L.l[i] = acc;
     vv = fma(acc, acc, vv);
   }
@@ -174,16 +174,21 @@ __device__ bool add_point32(const D32Params& P, L32& L, const int32_t* cl, int n
   if (!(v > 0.0)) return false;
   const double inv_d = 1.0 / sqrt(v);
   for (int k = tid; k < j; k += blockDim.x) {
-    double acc = 0.0;
-    for (int i = k; i < j; ++i) acc = fma(L.l[i], Lg[(int64_t)i * ld + k], acc);
-    const double rk = -acc * inv_d;
+    double a0 = 0.0, a1 = 0.0;
+    int i = k;
+    for (; i + 1 < j; i += 2) {
+      a0 = fma(L.l[i], Lg[(int64_t)i * ld + k], a0);
+      a1 = fma(L.l[i + 1], Lg[(int64_t)(i + 1) * ld + k], a1);
+    }
+    if (i < j) a0 = fma(L.l[i], Lg[(int64_t)i * ld + k], a0);
+    const double rk = -(a0 + a1) * inv_d;
     Lg[(int64_t)j * ld + k] = rk;
     L.Lf[j * L.ldf + k] = (float)rk;
   }
   if (tid == 0) {
     Lg[(int64_t)j * ld + j] = inv_d;
     L.Lf[j * L.ldf + j] = (float)inv_d;
-    L.kx[j] = corr64(L.S64 + j * p, L.xq, p, P.theta);
+    L.kx[j] = corr64_fast(L.S64 + j * p, L.xq, p, nit64);
     L.sel[j] = r;
     L.used[r] = 1;
   }

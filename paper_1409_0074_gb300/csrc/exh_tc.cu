@@ -167,6 +167,7 @@ __global__ void __launch_bounds__(XT_THREADS) exh_tc_kernel(XtParams P) {
   double* Lg = P.Linv + (int64_t)blockIdx.x * ld * ld;
   float* Kc = P.Kc + (int64_t)blockIdx.x * ld * nc_max;
   const float nit = (float)(-1.0 / P.theta);
+  const double nit64 = -1.0 / P.theta;
   const float onepg = (float)(1.0 + P.g);
   const unsigned items = P.count ? *P.count : (unsigned)P.M;
   uint32_t phase = 0;
@@ -206,13 +207,12 @@ __global__ void __launch_bounds__(XT_THREADS) exh_tc_kernel(XtParams P) {
       const double* c = P.X + (int64_t)cl[rr] * p;
       if (tid < p) S64[j * p + tid] = c[tid];
       __syncthreads();
-      for (int i = tid; i < j; i += XT_THREADS) kv[i] = corr64(S64 + i * p, S64 + j * p, p, P.theta);
+      for (int i = tid; i < j; i += XT_THREADS) kv[i] = corr64_fast(S64 + i * p, S64 + j * p, p, nit64);
       __syncthreads();
       double vv = 0.0;
       for (int i = tid; i < j; i += XT_THREADS) {
         const double* Li = Lg + (int64_t)i * ld;
-        double acc = 0.0;
-        for (int k = 0; k <= i; ++k) acc = fma(Li[k], kv[k], acc);
+        const double acc = dot64_ilp(Li, kv, i + 1);
         lv[i] = acc;
         vv = fma(acc, acc, vv);
       }
@@ -223,8 +223,14 @@ __global__ void __launch_bounds__(XT_THREADS) exh_tc_kernel(XtParams P) {
       for (int k = tid; k <= j; k += XT_THREADS) {
         double rk = inv_d;
         if (k < j) {
-          double acc = 0.0;
-          for (int i = k; i < j; ++i) acc = fma(lv[i], Lg[(int64_t)i * ld + k], acc);
+          double a0 = 0.0, a1 = 0.0;
+          int i = k;
+          for (; i + 1 < j; i += 2) {
+            a0 = fma(lv[i], Lg[(int64_t)i * ld + k], a0);
+            a1 = fma(lv[i + 1], Lg[(int64_t)(i + 1) * ld + k], a1);
+          }
+          if (i < j) a0 = fma(lv[i], Lg[(int64_t)i * ld + k], a0);
+          const double acc = a0 + a1;
           rk = -acc * inv_d;
         }
         Lg[(int64_t)j * ld + k] = rk;
@@ -234,7 +240,7 @@ __global__ void __launch_bounds__(XT_THREADS) exh_tc_kernel(XtParams P) {
         Blo[off] = xtf32((float)(rk - (double)h));
       }
       if (tid == 0) {
-        kx[j] = corr64(S64 + j * p, xq, p, P.theta);
+        kx[j] = corr64_fast(S64 + j * p, xq, p, nit64);
         sel[j] = rr;
         used[rr] = 1;
       }

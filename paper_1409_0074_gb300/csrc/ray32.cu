@@ -200,6 +200,7 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
   const double* xq = P.xref + loc * p;
 
   const float nit = (float)(-1.0 / P.theta);
+  const double nit64 = -1.0 / P.theta;
   const float onepg = (float)(1.0 + P.g);
 
   for (int i = lane; i < roff(ldn); i += 32) Lf[i] = 0.f;
@@ -221,13 +222,13 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
   // ---- append candidate rank rr to the design (FP64 factor row) ----
   auto add_point = [&](int rr) -> bool {
     const double* c64 = P.X + (int64_t)cl[rr] * p;
-    for (int i = lane; i < j; i += 32) kv64[i] = corr64(P.X + (int64_t)cl[sel[i]] * p, c64, p, P.theta);
+    for (int i = lane; i < j; i += 32)
+      kv64[i] = corr64_fast(P.X + (int64_t)cl[sel[i]] * p, c64, p, nit64);
     __syncwarp();
     double vv = 0.0;
     for (int i = lane; i < j; i += 32) {
       const double* Li = Lg + tri(i);
-      double acc = 0.0;
-      for (int k = 0; k <= i; ++k) acc = fma(Li[k], kv64[k], acc);
+      const double acc = dot64_ilp(Li, kv64, i + 1);
       l64[i] = acc;
       vv = fma(acc, acc, vv);
     }
@@ -239,8 +240,14 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
     double* Lj = Lg + tri(j);
     float* Lfj = Lf + roff(j);
     for (int k = lane; k < j; k += 32) {
-      double acc = 0.0;
-      for (int i = k; i < j; ++i) acc = fma(l64[i], Lg[tri(i) + k], acc);
+      double a0 = 0.0, a1 = 0.0;
+      int i = k;
+      for (; i + 1 < j; i += 2) {
+        a0 = fma(l64[i], Lg[tri(i) + k], a0);
+        a1 = fma(l64[i + 1], Lg[tri(i + 1) + k], a1);
+      }
+      if (i < j) a0 = fma(l64[i], Lg[tri(i) + k], a0);
+      const double acc = a0 + a1;
       const double rk = -acc * inv_d;
       Lj[k] = rk;
       Lfj[k] = (float)rk;
@@ -248,7 +255,7 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
     if (lane == 0) {
       Lj[j] = inv_d;
       Lfj[j] = (float)inv_d;
-      kx64[j] = corr64(c64, xq, p, P.theta);
+      kx64[j] = corr64_fast(c64, xq, p, nit64);
       sel[j] = rr;
       mask[rr >> 5] |= 1u << (rr & 31);
     }
@@ -511,8 +518,9 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
     for (int i = lane; i < ldn; i += 32) P.selected[loc * ldn + i] = (i < j) ? cl[sel[i]] : -1;
 }
 
+// at least 20 resident warps per SM (at most 102 registers per thread)
 template <int RP, int PP, int RW>
-__global__ void __launch_bounds__(RW * 32) ray32_kernel(RayParams P) {
+__global__ void __launch_bounds__(RW * 32, 20 / RW) ray32_kernel(RayParams P) {
   extern __shared__ __align__(16) float sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const WarpLayout lay = warp_layout(P.n_max, PP, RP, P.nc_max);
