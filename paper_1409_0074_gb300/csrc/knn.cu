@@ -15,6 +15,17 @@
 // Every true member of the N'-nearest set survives stage 1: at the end at
 // least N' points have d32 <= tau, so the N'-th smallest d64 is at most
 // tau + err, and any member has d32 <= d64 + err <= tau + 2 err.
+//
+// Pilot threshold (N >= 32 N').  Before the stream, knn_pilot estimates each
+// location's N'-th distance from a stride sample of S design points: with
+// lambda = S N'/N sample points expected inside it, the m-th smallest sample
+// distance, m = lambda + 4.5 sqrt(lambda) + 4, is above it except with
+// probability ~1e-5.  The stream starts with tau = that value instead of
+// infinity, so few points are buffered and the buffer rarely needs a
+// compaction.  The estimate is checked, not trusted: at the end at least N'
+// buffered points must lie at or below it (then the N'-th smallest d32 does
+// too, and every point that could belong was admitted); a location that fails
+// the check is streamed again with tau = infinity.
 #include <cfloat>
 #include <cstdint>
 
@@ -172,13 +183,132 @@ __device__ int warp_compact(KnnEntry* e, int cnt, float keep) {
   return out;
 }
 
+// squared FP32 distance of a design row to the 4 locations of a warp, in the
+// stream's form |q|^2 + |x|^2 - 2 q.x
+template <int PP>
+__device__ __forceinline__ void knn_d4(const float (&qf)[KNN_QW][PP], const float (&nq)[KNN_QW],
+                                       const float (&xv)[PP], float nxp, float (&d)[KNN_QW]) {
+#pragma unroll
+  for (int a = 0; a < KNN_QW; ++a) {
+    float dot = 0.f;
+#pragma unroll
+    for (int k = 0; k < PP; ++k) dot = fmaf(qf[a][k], xv[k], dot);
+    d[a] = fmaf(-2.f, dot, nq[a] + nxp);
+  }
+}
+
+// first bin (of 256 per location, lane l owning bins 8l..8l+7) at which the
+// running count reaches k; *below receives the count before that bin
+__device__ __forceinline__ int warp_bin_of_kth(const uint32_t* h, int k, int* below) {
+  const int lane = threadIdx.x & 31;
+  uint32_t c[8], tot = 0;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) { c[b] = h[lane * 8 + b]; tot += c[b]; }
+  uint32_t incl = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const uint32_t excl = incl - tot;
+  const int found = ((int)excl < k && (int)incl >= k);
+  const uint32_t fm = __ballot_sync(0xffffffffu, found);
+  int bin = 255, run_out = 0;
+  if (found) {
+    uint32_t run = excl;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      if ((int)(run + c[b]) >= k) { bin = lane * 8 + b; run_out = (int)run; break; }
+      run += c[b];
+    }
+  }
+  const int src = fm ? __ffs(fm) - 1 : 0;
+  *below = __shfl_sync(0xffffffffu, run_out, src);
+  return fm ? __shfl_sync(0xffffffffu, bin, src) : -1;
+}
+
+// Pilot thresholds: per location the upper edge of the 2^-8-wide bin (by the
+// float bit pattern: exponent, then the top 8 mantissa bits) that holds the
+// m-th smallest d32 of the S sample rows i * (N / S); +inf where the pilot
+// does not apply (m > S, or more than cap - 2 tiles expected below it).
+template <int PP>
+__global__ void __launch_bounds__(KNN_WARPS * 32)
+knn_pilot(const float* __restrict__ Xf, const float* __restrict__ nx, int64_t N, int64_t S, int p,
+          const double* __restrict__ xref, int64_t M, const double* __restrict__ center,
+          int nc_max, const int32_t* __restrict__ nc_loc, int cap, float* __restrict__ thr_out) {
+  __shared__ uint32_t hist[KNN_WARPS][KNN_QW][256];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t q0 = (int64_t)blockIdx.x * (KNN_WARPS * KNN_QW) + warp * KNN_QW;
+  float qf[KNN_QW][PP], nq[KNN_QW];
+  int m[KNN_QW];
+  const int64_t stride = N / S;
+#pragma unroll
+  for (int a = 0; a < KNN_QW; ++a) {
+    const int64_t q = q0 + a;
+    const bool live = q < M;
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < PP; ++k) {
+      float v = 0.f;
+      if (live && k < p) v = (float)(xref[q * p + k] - center[k]);
+      qf[a][k] = v;
+      acc = fmaf(v, v, acc);
+    }
+    nq[a] = acc;
+    const int nc = live ? (nc_loc ? nc_loc[q] : nc_max) : 0;
+    const float lam = (float)S * (float)nc / (float)N;
+    m[a] = (int)ceilf(lam + 4.5f * sqrtf(lam) + 4.f);
+    // expected admitted points m N / S must leave two tiles of room
+    if (!live || m[a] > S || (double)m[a] * (double)N / (double)S > (double)(cap - 2 * LAGP_KNN_TILE))
+      m[a] = 0;
+  }
+  uint32_t b1[KNN_QW];
+  int below[KNN_QW];
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int i = lane; i < KNN_QW * 256; i += 32) (&hist[warp][0][0])[i] = 0u;
+    __syncwarp();
+    for (int64_t i = lane; i < S; i += 32) {
+      const int64_t row = i * stride;
+      float xv[PP];
+#pragma unroll
+      for (int k = 0; k < PP; k += 4) {
+        const float4 v4 = __ldg(reinterpret_cast<const float4*>(Xf + row * PP + k));
+        xv[k] = v4.x; xv[k + 1] = v4.y; xv[k + 2] = v4.z; xv[k + 3] = v4.w;
+      }
+      float d[KNN_QW];
+      knn_d4<PP>(qf, nq, xv, __ldg(nx + row), d);
+#pragma unroll
+      for (int a = 0; a < KNN_QW; ++a) {
+        const uint32_t bits = __float_as_uint(fmaxf(d[a], 0.f));
+        if (pass == 0) atomicAdd(&hist[warp][a][bits >> 23], 1u);
+        else if ((bits >> 23) == b1[a]) atomicAdd(&hist[warp][a][(bits >> 15) & 255u], 1u);
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int a = 0; a < KNN_QW; ++a) {
+      if (pass == 0) {
+        const int b = warp_bin_of_kth(hist[warp][a], m[a] > 0 ? m[a] : 1, &below[a]);
+        b1[a] = b < 0 ? 0u : (uint32_t)b;
+      } else {
+        int dummy = 0;
+        const int b = warp_bin_of_kth(hist[warp][a], m[a] > 0 ? m[a] - below[a] : 1, &dummy);
+        float thr = __uint_as_float((b1[a] << 23) | ((uint32_t)(b < 0 ? 255 : b) << 15) | 0x7fffu);
+        if (m[a] == 0 || b < 0 || !(thr < __int_as_float(0x7f800000))) thr = __int_as_float(0x7f800000);
+        if (lane == 0 && q0 + a < M) thr_out[q0 + a] = thr;
+      }
+    }
+    __syncwarp();
+  }
+}
+
 template <int PP>
 __global__ void __launch_bounds__(KNN_WARPS * 32, 3)
 knn_stream(const float* __restrict__ Xf, const float* __restrict__ nx, int64_t N, int64_t ntiles,
            int p, const double* __restrict__ xref, int64_t M, const double* __restrict__ center,
            const unsigned* __restrict__ maxn2_bits, int nc_max, const int32_t* __restrict__ nc_loc,
            int cap, KnnEntry* __restrict__ buf, int32_t* __restrict__ cnt_out,
-           unsigned* __restrict__ status) {
+           unsigned* __restrict__ status, const float* __restrict__ pilot, int redo) {
   extern __shared__ __align__(128) unsigned char smem[];
   float* tile = reinterpret_cast<float*>(smem);                    // [2][TILE][PP]
   float* tnorm = tile + 2 * LAGP_KNN_TILE * PP;                     // [2][TILE]
@@ -192,10 +322,15 @@ knn_stream(const float* __restrict__ Xf, const float* __restrict__ nx, int64_t N
   int cnt[KNN_QW], ncq[KNN_QW];
   bool live[KNN_QW];
   const float rmax = sqrtf(__uint_as_float(*maxn2_bits)) * 1.0001f;
+  const float inf = __int_as_float(0x7f800000);
+  bool any = false;
 #pragma unroll
   for (int a = 0; a < KNN_QW; ++a) {
     int64_t q = q0 + a;
     live[a] = q < M;
+    // redo pass: only the locations whose pilot threshold failed its check
+    if (redo && live[a]) live[a] = cnt_out[q] < 0;
+    any = any || live[a];
     float acc = 0.f;
 #pragma unroll
     for (int k = 0; k < PP; ++k) {
@@ -207,10 +342,12 @@ knn_stream(const float* __restrict__ Xf, const float* __restrict__ nx, int64_t N
     nq[a] = acc;
     float r = rmax + sqrtf(acc) * 1.0001f;
     err[a] = (float)(p + 12) * 0x1p-24f * 1.25f * r * r;
-    keep[a] = live[a] ? __int_as_float(0x7f800000) : -1.f;
+    const float thr = (live[a] && pilot) ? pilot[q] : inf;
+    keep[a] = live[a] ? (thr < inf ? __fadd_ru(thr, 2.f * err[a]) : inf) : -1.f;
     cnt[a] = 0;
     ncq[a] = live[a] ? (nc_loc ? nc_loc[q] : nc_max) : 0;
   }
+  if (!__syncthreads_or(any)) return;   // a redo pass with nothing to redo here
 
   const uint32_t tile_bytes = LAGP_KNN_TILE * PP * sizeof(float);
   const uint32_t norm_bytes = LAGP_KNN_TILE * sizeof(float);
@@ -290,7 +427,7 @@ knn_stream(const float* __restrict__ Xf, const float* __restrict__ nx, int64_t N
         __syncwarp();
         uint32_t kb = warp_select_kth(e, c, ncq[a], hist + warp * 256);
         float kth = __uint_as_float(kb);
-        keep[a] = __fadd_ru(kth, 2.f * err[a]);
+        keep[a] = fminf(keep[a], __fadd_ru(kth, 2.f * err[a]));
         cnt[a] = warp_compact(e, c, keep[a]);
         if (cnt[a] > cap - LAGP_KNN_TILE && lane == 0) atomicOr(status, LAGP_DEV_KNN_OVERFLOW);
       }
@@ -309,6 +446,18 @@ knn_stream(const float* __restrict__ Xf, const float* __restrict__ nx, int64_t N
     KnnEntry* e = buf + (q0 + a) * (int64_t)cap;
     int c = min(cnt[a], cap);
     __syncwarp();
+    const float thr = pilot ? pilot[q0 + a] : inf;
+    if (thr < inf) {
+      // the pilot threshold holds if at least N' buffered points lie at or below it
+      int below = 0;
+      for (int i = lane; i < c; i += 32) below += (e[i].d <= thr) ? 1 : 0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) below += __shfl_xor_sync(0xffffffffu, below, o);
+      if (below < ncq[a]) {
+        if (lane == 0) cnt_out[q0 + a] = -1;   // stream this location again
+        continue;
+      }
+    }
     if (c >= ncq[a] && ncq[a] > 0) {
       uint32_t kb = warp_select_kth(e, c, ncq[a], hist + warp * 256);
       c = warp_compact(e, c, __fadd_ru(__uint_as_float(kb), 2.f * err[a]));
@@ -387,7 +536,8 @@ size_t knn_smem_stream(int PP) {
 // for distances within the error margin of the N'-th.  A power of two, as the
 // bitonic sort of knn_rank wants.
 int knn_cap(int nc_max) {
-  const int need = nc_max + LAGP_KNN_TILE + (nc_max / 2 > 64 ? nc_max / 2 : 64);
+  // with the pilot threshold about 2.2 N' points are admitted
+  const int need = (5 * nc_max) / 2 + LAGP_KNN_TILE;
   int cap = 512;
   while (cap < need) cap <<= 1;
   return cap;
@@ -417,20 +567,37 @@ cudaError_t launch_knn(const double* X, int64_t N, int p, int PP, int64_t Npad,
   const int qpb = KNN_WARPS * KNN_QW;
   dim3 grid((unsigned)((M + qpb - 1) / qpb));
   size_t sm = knn_smem_stream(PP);
+  // pilot thresholds where the design is large against N'
+  const bool pilot = N >= (int64_t)32 * nc_max;
+  const int64_t S = N / 16 < 16384 ? N / 16 : 16384;
+  KnnEntry* kbuf = reinterpret_cast<KnnEntry*>(ws.knn_buf);
   cudaError_t err;
   switch (PP) {
-#define KNN_CASE(V)                                                                        \
-  case V:                                                                                  \
-    err = cudaFuncSetAttribute(knn_stream<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                               (int)sm);                                                   \
-    if (err != cudaSuccess) return err;                                                    \
-    prof_begin("knn_stream", s);                                                           \
-    knn_stream<V><<<grid, KNN_WARPS * 32, sm, s>>>(ws.Xf, ws.nx, N, ntiles, p, xref, M,    \
-                                                   ws.center, ws.maxn2, nc_max, nc_loc,    \
-                                                   cap, reinterpret_cast<KnnEntry*>(       \
-                                                            ws.knn_buf),                   \
-                                                   ws.knn_cnt, ws.status);                 \
-    prof_end(s);                                                                           \
+#define KNN_CASE(V)                                                                          \
+  case V:                                                                                    \
+    err = cudaFuncSetAttribute(knn_stream<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                               (int)sm);                                                     \
+    if (err != cudaSuccess) return err;                                                      \
+    if (pilot) {                                                                             \
+      prof_begin("knn_pilot", s);                                                            \
+      knn_pilot<V><<<grid, KNN_WARPS * 32, 0, s>>>(ws.Xf, ws.nx, N, S, p, xref, M, ws.center, \
+                                                   nc_max, nc_loc, cap, ws.knn_thr);         \
+      prof_end(s);                                                                           \
+    }                                                                                        \
+    prof_begin("knn_stream", s);                                                             \
+    knn_stream<V><<<grid, KNN_WARPS * 32, sm, s>>>(ws.Xf, ws.nx, N, ntiles, p, xref, M,      \
+                                                   ws.center, ws.maxn2, nc_max, nc_loc, cap, \
+                                                   kbuf, ws.knn_cnt, ws.status,              \
+                                                   pilot ? ws.knn_thr : nullptr, 0);         \
+    prof_end(s);                                                                             \
+    if (pilot) {                                                                             \
+      prof_begin("knn_stream_redo", s);                                                      \
+      knn_stream<V><<<grid, KNN_WARPS * 32, sm, s>>>(ws.Xf, ws.nx, N, ntiles, p, xref, M,    \
+                                                     ws.center, ws.maxn2, nc_max, nc_loc,    \
+                                                     cap, kbuf, ws.knn_cnt, ws.status,       \
+                                                     nullptr, 1);                            \
+      prof_end(s);                                                                           \
+    }                                                                                        \
     break;
     KNN_CASE(4)
     KNN_CASE(8)

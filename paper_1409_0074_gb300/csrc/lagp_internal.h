@@ -20,7 +20,8 @@ struct Workspace {
   float* Xf;            // [Npad][PP] centred FP32 design, PP = p rounded up to 4
   float* nx;            // [Npad] squared norms of Xf rows
   void* knn_buf;        // [chunk][cap] (float d32, int32 index) candidate buffers
-  int32_t* knn_cnt;     // [chunk] surviving buffer entries
+  int32_t* knn_cnt;     // [chunk] surviving buffer entries (-1: stream again)
+  float* knn_thr;       // [chunk] pilot thresholds of the kNN stream
   int32_t* cand;        // [chunk][nc_max] candidate design indices, nearest first
   double* state64;      // FP64 state: FP64 form, exhaustive: [chunk][nc_max][n_max]
                         // correlation cache; FP32 form: per slot, L^{-1} and its vectors

@@ -101,6 +101,47 @@ def test_knn_bit_exact(lagp, p, N, M, nc):
         np.testing.assert_array_equal(cand[m], idx)
 
 
+def test_knn_pilot_threshold_failure_is_streamed_again(lagp):
+    """For N >= 32 N' the stream starts from a threshold estimated on the
+    stride sample of rows i * (N / S).  Here those rows are exactly the points
+    clustered at the locations, so the estimate is far too tight; the check at
+    the end of the stream must catch it and the location must be streamed
+    again: the candidate lists still equal the oracle's."""
+    rng = np.random.default_rng(21)
+    N, p, nc, M = 40000, 3, 1000, 24
+    X = rng.random((N, p)) * 10.0                    # far away
+    S = min(16384, N // 16)
+    rows = np.arange(S) * (N // S)
+    X[rows] = 5.0 + 0.05 * rng.standard_normal((S, p))   # sampled rows: a tight cluster
+    Xref = 5.0 + 0.05 * rng.standard_normal((M, p))
+    cand = knn_gpu(lagp, X, Xref, nc)
+    for m in range(M):
+        idx, _ = oracle.knn(X, Xref[m], nc)
+        np.testing.assert_array_equal(cand[m], idx)
+
+
+def test_knn_large_design_uneven_nclose(lagp):
+    """Pilot thresholds with per-location N' (the uneven workload's kNN)."""
+    import torch
+    rng = np.random.default_rng(8)
+    N, p, M = 300000, 8, 40
+    X = rng.random((N, p))
+    Xref = rng.random((M, p))
+    ncl = rng.integers(300, 2001, M).astype(np.int32)
+    nmax = int(ncl.max())
+    Y = np.zeros(N)
+    out = lagp.predict(to_dev(X), to_dev(Y), to_dev(Xref), 6, 20, nmax, 1.0, 1e-6,
+                       search="exhaustive", precision="fp32", want_trace=True,
+                       n_loc=to_dev(np.full(M, 20, np.int32), torch.int32),
+                       nclose_loc=to_dev(ncl, torch.int32))
+    torch.cuda.synchronize()
+    sel = out["selected"].cpu().numpy()
+    for m in range(M):
+        idx, _ = oracle.knn(X, Xref[m], int(ncl[m]))
+        np.testing.assert_array_equal(sel[m, :6], idx[:6])     # the n0 nearest start the design
+        assert set(sel[m][sel[m] >= 0]) <= set(idx.tolist())   # every pick is a candidate
+
+
 def test_knn_exact_ties_go_to_lower_index(lagp):
     rng = np.random.default_rng(5)
     X = rng.integers(0, 7, (6000, 3)).astype(np.float64)   # many duplicates and ties
