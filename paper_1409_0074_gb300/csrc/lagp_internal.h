@@ -25,7 +25,8 @@ struct Workspace {
   int32_t* cand;        // [chunk][nc_max] candidate design indices, nearest first
   double* state64;      // FP64 state: FP64 form, exhaustive: [chunk][nc_max][n_max]
                         // correlation cache; FP32 form: per slot, L^{-1} and its vectors
-  float* state32;       // FP32 form, exhaustive: [slots][n_max][nc_max] correlation cache
+  float* state32;       // FP32 form: exhaustive [slots][n_max][nc_max] correlation cache;
+                        // ray [warp slots][nc_max][PP] gathered candidate rows
   unsigned* queue;      // [4] work counters of the persistent kernels
   int32_t* order;       // [2][chunk] work order (largest local designs first), two parts
   unsigned* order_hist; // [2][256] cost-bucket counts, then offsets
@@ -37,7 +38,7 @@ struct Workspace {
 // Warp slots of the persistent ray kernel and CTA slots of the persistent
 // exhaustive kernels: their FP64 / correlation scratch is per slot, so a
 // launch holds at most this many locations' state at a time.
-#define RAY_SLOTS 16384
+#define RAY_SLOTS 6144
 #define EXH_SLOTS 2048
 int ray32_slots(int64_t chunk);
 int exh_slots(int64_t chunk);
