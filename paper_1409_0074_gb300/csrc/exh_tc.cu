@@ -18,8 +18,14 @@
 // FP64 state (the partitioned update in factored form, Sec 2.2): L_j^{-1} in
 // global memory, grown by one row per step, and z, L^{-1} y; the predictive
 // equations (Eq. predgp, preds2) at the end.  Each new row of L^{-1} is also
-// written, split into TF32 hi + lo, into the B operand in shared memory; the
-// correlation cache gains one row (N' exponentials) per step.
+// written, split into TF32 hi + lo, into the B operand in shared memory.
+//
+// The correlation cache is kept in global memory already in the A operand's
+// form: per 128-candidate tile, TF32 hi and lo blocks in the canonical K-major
+// layout (XT_KMAX columns); each step writes one column (N' exponentials).
+// A tile's operand then arrives by bulk copies (TMA), 16 row groups of jk/4
+// core matrices each for hi and lo, and the copy of the next tile runs while
+// the epilogue reads the current tile's scores from TMEM.
 #include <cstdint>
 
 #include "common.cuh"
@@ -50,12 +56,14 @@ struct XtParams {
   double* tie_gap;
   int32_t* nevals;
   double* Linv;          // [slots][n_max][n_max]
-  float* Kc;             // [slots][n_max][nc_max]
+  float* Kc;             // [slots][ceil(nc_max / 128)] tiles of 2 x 128 x XT_KMAX floats
   unsigned* status;
   unsigned* queue;       // work counter (zero at launch)
   const int32_t* order;  // item -> location, or null
   const unsigned* count; // items (device), or null (M)
 };
+
+#define XT_TILE_FLOATS (128 * XT_KMAX)   // one of hi / lo of a 128-candidate tile
 
 // canonical no-swizzle K-major layout with XT_KMAX columns per row
 __device__ __forceinline__ uint32_t xcanon(int row, int k) {
@@ -145,13 +153,15 @@ __global__ void __launch_bounds__(XT_THREADS) exh_tc_kernel(XtParams P) {
   int* sel = ired + 8;                                                // [XT_KMAX]
   unsigned char* used = reinterpret_cast<unsigned char*>(sel + XT_KMAX);
   uint64_t* bar = reinterpret_cast<uint64_t*>(
-      (reinterpret_cast<uintptr_t>(used + nc_max) + 15) & ~(uintptr_t)15);
-  uint32_t* tbase = reinterpret_cast<uint32_t*>(bar + 1);
+      (reinterpret_cast<uintptr_t>(used + nc_max) + 15) & ~(uintptr_t)15);   // MMA done
+  uint64_t* bar_a = bar + 1;                                                  // A tile loaded
+  uint32_t* tbase = reinterpret_cast<uint32_t*>(bar + 2);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   unsigned* s_item = tbase + 1;
   if (tid == 0) {
     mbar_init(bar, 1);
+    mbar_init(bar_a, 1);
     fence_mbar_init();
   }
   if (warp == 0) {
@@ -163,9 +173,17 @@ __global__ void __launch_bounds__(XT_THREADS) exh_tc_kernel(XtParams P) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t taddr = *tbase;
-  // scratch of this CTA slot
+  // scratch of this CTA slot; the correlation tiles start zeroed, so that the
+  // columns past j and the rows past N' that the MMAs read hold finite values
   double* Lg = P.Linv + (int64_t)blockIdx.x * ld * ld;
-  float* Kc = P.Kc + (int64_t)blockIdx.x * ld * nc_max;
+  const int ntc = (nc_max + 127) / 128;
+  float* Kc = P.Kc + (int64_t)blockIdx.x * ntc * 2 * XT_TILE_FLOATS;
+  for (int64_t i = tid; i < (int64_t)ntc * 2 * XT_TILE_FLOATS / 4; i += XT_THREADS)
+    reinterpret_cast<float4*>(Kc)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  __syncthreads();
+  uint32_t phase_a = 0;
+  bool a_pending = false, m_pending = false;   // a bulk copy / MMA not yet waited for
   const float nit = (float)(-1.0 / P.theta);
   const double nit64 = -1.0 / P.theta;
   const float onepg = (float)(1.0 + P.g);
@@ -258,10 +276,21 @@ __global__ void __launch_bounds__(XT_THREADS) exh_tc_kernel(XtParams P) {
         zy[j] = zyy;
         zf[j] = (float)zz;
       }
-      // correlation cache row j: K(c_r, S_j) for every candidate
+      // correlation cache column j: K(c_r, S_j) for every candidate, as A operand
+      // (TF32 hi / lo) of its tile; then visible to the bulk copies
       const float* sj = P.Xf + (int64_t)cl[rr] * PP;
-      for (int q = tid; q < nc; q += XT_THREADS)
-        Kc[(int64_t)j * nc_max + q] = __expf(sqdist_row32(P.Xf + (int64_t)cl[q] * PP, sj, PP) * nit);
+      for (int q = tid; q < nc; q += XT_THREADS) {
+        const float kv = __expf(sqdist_row32(P.Xf + (int64_t)cl[q] * PP, sj, PP) * nit);
+        const float h = xtf32(kv);
+        float* tile = Kc + (int64_t)(q >> 7) * 2 * XT_TILE_FLOATS;
+        const uint32_t off = xcanon(q & 127, j) >> 2;
+        tile[off] = h;
+        tile[XT_TILE_FLOATS + off] = xtf32(kv - h);
+      }
+      // this step's generic writes (the B row in shared memory, the cache column
+      // in global memory) become visible to the tensor core and the bulk copies
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("fence.proxy.async.global;" ::: "memory");
       __syncthreads();
       ++j;
       return true;
@@ -276,26 +305,38 @@ __global__ void __launch_bounds__(XT_THREADS) exh_tc_kernel(XtParams P) {
                              ((uint32_t)(128 >> 4) << 24);
       float best = -1.f, second = -1.f;
       int bi = -1;
-      for (int base = 0; base < nc; base += 128) {
-        // A operand: this thread's candidate row, hi / lo, zero past j
+      // A tile t: 16 row groups x (jk / 4) core matrices of hi and of lo, one bulk
+      // copy each, issued by the 32 lanes of warp 0 (lane l: row group l % 16,
+      // hi for l < 16, lo above)
+      const uint32_t rg_bytes = (uint32_t)jk * 32u;
+      auto load_a = [&](int t) {
+        a_pending = true;
+        if (warp == 0) {
+          if (lane == 0) mbar_expect_tx(bar_a, 32u * rg_bytes);
+          __syncwarp();
+          const int rg = lane & 15, part = lane >> 4;
+          const float* src = Kc + (int64_t)t * 2 * XT_TILE_FLOATS + part * XT_TILE_FLOATS + rg * (XT_KMAX / 4) * 32;
+          float* dst = (part ? Alo : Ahi) + rg * (XT_KMAX / 4) * 32;
+          bulk_g2s(dst, src, rg_bytes, bar_a);
+        }
+      };
+      const int ntile = (nc + 127) >> 7;
+      load_a(0);
+      for (int t = 0; t < ntile; ++t) {
+        const int base = t << 7;
         const int r = base + tid;
         const bool live = r < nc;
-  #pragma unroll 4
-        for (int k = 0; k < jk; k += 4) {
-          float4 h, l;
-          float vals[4];
-  #pragma unroll
-          for (int u = 0; u < 4; ++u)
-            vals[u] = (live && k + u < j) ? Kc[(int64_t)(k + u) * nc_max + r] : 0.f;
-          h.x = xtf32(vals[0]); h.y = xtf32(vals[1]); h.z = xtf32(vals[2]); h.w = xtf32(vals[3]);
-          l.x = xtf32(vals[0] - h.x); l.y = xtf32(vals[1] - h.y);
-          l.z = xtf32(vals[2] - h.z); l.w = xtf32(vals[3] - h.w);
-          const uint32_t off = xcanon(tid, k) >> 2;
-          *reinterpret_cast<float4*>(Ahi + off) = h;
-          *reinterpret_cast<float4*>(Alo + off) = l;
+        // tile t's operand in shared memory, then its MMAs
+        bool got = mbar_wait(bar_a, phase_a);
+        if (!__syncthreads_and(got)) {
+          if (tid == 0) atomicOr(P.status, LAGP_DEV_TIMEOUT);
+          ok = false;
+          timed_out = true;
+          break;
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
+        phase_a ^= 1u;
+        a_pending = false;
+        m_pending = true;
         if (tid == 0) {
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo);
@@ -311,13 +352,16 @@ __global__ void __launch_bounds__(XT_THREADS) exh_tc_kernel(XtParams P) {
                        : "memory");
         }
         bool done = mbar_wait(bar, phase);
-        phase ^= 1u;
         if (!__syncthreads_and(done)) {
           if (tid == 0) atomicOr(P.status, LAGP_DEV_TIMEOUT);
           ok = false;
           timed_out = true;
           break;
         }
+        phase ^= 1u;
+        m_pending = false;
+        // the MMAs have read the A buffer: the next tile's copy overlaps the epilogue
+        if (t + 1 < ntile) load_a(t + 1);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // epilogue: row tid of W
         float vs = 0.f, ns = 0.f;
@@ -396,6 +440,9 @@ __global__ void __launch_bounds__(XT_THREADS) exh_tc_kernel(XtParams P) {
     if (P.selected)
       for (int i = tid; i < ldo; i += XT_THREADS) P.selected[loc * ldo + i] = (i < j) ? cl[sel[i]] : -1;
   }
+  // after a timeout: wait (bounded) for the copy or MMAs still in flight
+  if (a_pending) mbar_wait(bar_a, phase_a);
+  if (m_pending) mbar_wait(bar, phase);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
@@ -406,6 +453,8 @@ __global__ void __launch_bounds__(XT_THREADS) exh_tc_kernel(XtParams P) {
 
 int exh_tc_max_n() { return XT_KMAX; }
 
+size_t exh_tc_cache_floats(int nc_max) { return (size_t)((nc_max + 127) / 128) * 2 * XT_TILE_FLOATS; }
+
 cudaError_t launch_exh_tc(const DesignArgs& a, cudaStream_t s) {
   XtParams P;
   P.X = a.X; P.Y = a.Y; P.p = a.p; P.PP = a.PP; P.Xf = a.ws->Xf; P.xref = a.xref; P.M = a.M;
@@ -415,7 +464,7 @@ cudaError_t launch_exh_tc(const DesignArgs& a, cudaStream_t s) {
   P.Linv = a.ws->state64; P.Kc = a.ws->state32; P.status = a.ws->status;
   P.queue = a.ws->queue + 1; P.order = a.order; P.count = a.count;
   const size_t small = (size_t)((a.nc_max + 3) & ~3) * 4 + XT_KMAX * 4 + (size_t)XT_KMAX * a.p * 8 +
-                       5 * XT_KMAX * 8 + 8 * 8 + 8 * 4 + 8 * 4 + XT_KMAX * 4 + a.nc_max + 64;
+                       5 * XT_KMAX * 8 + 8 * 8 + 8 * 4 + 8 * 4 + XT_KMAX * 4 + a.nc_max + 96;
   const size_t sm = 1024 + XtSmem::END + small;
   cudaError_t err =
       cudaFuncSetAttribute(exh_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -50,11 +50,14 @@ size_t layout_request(const Shape& sh, void* base, Workspace* ws) {
     if (sh.search == LAGP_EXHAUSTIVE) s64 = sizeof(double) * ch * sh.n_max * sh.nc_max;
   } else if (sh.search == LAGP_RAY) {
     s64 = sizeof(double) * ray32_slots(ch) * ray32_g64_doubles(sh.n_max);
-    s32 = sizeof(float) * ray32_slots(ch) * sh.nc_max * sh.PP;   // gathered candidate rows
   } else {
     const size_t slots = exh_slots(ch);
     s64 = sizeof(double) * slots * sh.n_max * sh.n_max;
-    s32 = sizeof(float) * slots * sh.n_max * sh.nc_max;
+    // correlation cache: [n_max][nc_max] (CUDA-core scorer) or operand tiles
+    // (tensor-core scorer), the larger
+    size_t per = (size_t)sh.n_max * sh.nc_max;
+    if (exh_tc_cache_floats(sh.nc_max) > per) per = exh_tc_cache_floats(sh.nc_max);
+    s32 = sizeof(float) * slots * per;
   }
   w->state64 = static_cast<double*>(c.take(s64));
   w->state32 = static_cast<float*>(c.take(s32));

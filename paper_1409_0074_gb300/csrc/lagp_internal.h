@@ -25,8 +25,7 @@ struct Workspace {
   int32_t* cand;        // [chunk][nc_max] candidate design indices, nearest first
   double* state64;      // FP64 state: FP64 form, exhaustive: [chunk][nc_max][n_max]
                         // correlation cache; FP32 form: per slot, L^{-1} and its vectors
-  float* state32;       // FP32 form: exhaustive [slots][n_max][nc_max] correlation cache;
-                        // ray [warp slots][nc_max][PP] gathered candidate rows
+  float* state32;       // FP32 form, exhaustive: [slots][n_max][nc_max] correlation cache
   unsigned* queue;      // [4] work counters of the persistent kernels
   int32_t* order;       // [2][chunk] work order (largest local designs first), two parts
   unsigned* order_hist; // [2][256] cost-bucket counts, then offsets
@@ -39,9 +38,11 @@ struct Workspace {
 // exhaustive kernels: their FP64 / correlation scratch is per slot, so a
 // launch holds at most this many locations' state at a time.
 #define RAY_SLOTS 6144
-#define EXH_SLOTS 2048
+#define EXH_SLOTS 1024
 int ray32_slots(int64_t chunk);
 int exh_slots(int64_t chunk);
+// floats of the tensor-core scorer's correlation cache per CTA slot
+size_t exh_tc_cache_floats(int nc_max);
 
 // Launch choices of the FP32-scoring kernels (picked by laGP_autotune, else
 // the defaults).  They schedule work only: no choice changes any result.

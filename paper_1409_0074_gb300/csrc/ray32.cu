@@ -56,7 +56,6 @@ struct RayParams {
   int32_t* nevals;
   double* g64;          // per warp slot: packed L^{-1} (n(n+1)/2) then kx, z, zy, kvec, l (n each)
   int64_t g64_stride;
-  float* cf;            // per warp slot: the location's candidates' FP32 rows [nc_max][PP]
   unsigned* status;
   unsigned* queue;      // work counter (zero at launch)
   const int32_t* order; // item -> location, or null (identity)
@@ -169,7 +168,7 @@ enum { PH_ALC0 = 0, PH_FIRST = 1, PH_ITER = 2, PH_DONE = 3 };
 // One location, by one warp, in the warp's shared-memory region and FP64 slot.
 template <int RP, int PP>
 __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t loc, float* base,
-                                               double* Lg, float* cf) {
+                                               double* Lg) {
   constexpr int G = 32 / RP;
   const int lane = threadIdx.x & 31;
   const int p = P.p, ldn = P.n_max, R = P.R;
@@ -215,14 +214,6 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
   }
   if (P.tie_gap) for (int i = lane; i < ldn; i += 32) P.tie_gap[loc * ldn + i] = 0.0;
   if (P.nevals) for (int i = lane; i < ldn; i += 32) P.nevals[loc * ldn + i] = 0;
-  // the candidates' FP32 rows, gathered once into the slot in rank order: the
-  // snap of every step then reads them contiguously
-  for (int rr = lane; rr < nc; rr += 32) {
-    const float4* src = reinterpret_cast<const float4*>(P.Xf + (int64_t)cl[rr] * PP);
-    float4* dst = reinterpret_cast<float4*>(cf + rr * PP);
-#pragma unroll
-    for (int k4 = 0; k4 < PP / 4; ++k4) dst[k4] = src[k4];
-  }
   __syncwarp();
 
   int j = 0;
@@ -268,7 +259,7 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
       sel[j] = rr;
       mask[rr >> 5] |= 1u << (rr & 31);
     }
-    if (lane < PP) Sf[j * PP + lane] = cf[rr * PP + lane];
+    if (lane < PP) Sf[j * PP + lane] = P.Xf[(int64_t)cl[rr] * PP + lane];
     __syncwarp();
     double zz = 0.0, zyy = 0.0;
     for (int k = lane; k <= j; k += 32) {
@@ -333,7 +324,7 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
     const bool ray_live = r < R;
     float len2 = 0.f;
     if (ray_live) {
-      const float* a = cf + starts[r] * PP;
+      const float* a = P.Xf + (int64_t)cl[starts[r]] * PP;
       float tau = 1.f;
       for (int k = 0; k < p; ++k) {
         const float dk = 10.f * (a[k] - xf[k]);
@@ -468,7 +459,7 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
       for (int wd = 0; wd < nw; ++wd) {
         const int rr = wd * 32 + lane;
         if (rr < nc && !(mask[wd] & bit)) {
-          const float* c = cf + rr * PP;
+          const float* c = P.Xf + (int64_t)cl[rr] * PP;
           bool same = true;
           float d = 0.f;
 #pragma unroll
@@ -534,16 +525,14 @@ __global__ void __launch_bounds__(RW * 32, 20 / RW) ray32_kernel(RayParams P) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const WarpLayout lay = warp_layout(P.n_max, PP, RP, P.nc_max);
   float* base = sm + (size_t)warp * (lay.bytes / 4);
-  const int64_t slot = (int64_t)blockIdx.x * RW + warp;
-  double* Lg = P.g64 + slot * P.g64_stride;
-  float* cf = P.cf + slot * (int64_t)P.nc_max * PP;
+  double* Lg = P.g64 + ((int64_t)blockIdx.x * RW + warp) * P.g64_stride;
   const unsigned items = P.count ? *P.count : (unsigned)P.M;
   for (;;) {
     unsigned it = 0;
     if (lane == 0) it = atomicAdd(P.queue, 1u);
     it = __shfl_sync(0xffffffffu, it, 0);
     if (it >= items) break;
-    ray32_location<RP, PP>(P, P.order ? (int64_t)P.order[it] : (int64_t)it, base, Lg, cf);
+    ray32_location<RP, PP>(P, P.order ? (int64_t)P.order[it] : (int64_t)it, base, Lg);
     __syncwarp();
   }
 }
@@ -579,7 +568,6 @@ cudaError_t launch_ray32(const DesignArgs& a, cudaStream_t s) {
   P.hi = a.ws->hi; P.center = a.ws->center; P.mean = a.mean; P.s2 = a.s2;
   P.selected = a.selected; P.tie_gap = a.tie_gap; P.nevals = a.nevals; P.g64 = a.ws->state64;
   P.g64_stride = (int64_t)ray32_g64_doubles(a.n_max); P.status = a.ws->status;
-  P.cf = a.ws->state32;
   P.queue = a.ws->queue; P.order = a.order; P.count = a.count;
   int RP = 2;
   while (RP < a.nrays) RP <<= 1;
