@@ -19,6 +19,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 UNITS = {
     "knn.cu": [],
+    "knn_tc.cu": [],
     "design_fp64.cu": ["--fmad=false"],
     "design_fp32.cu": [],
     "ray32.cu": [],

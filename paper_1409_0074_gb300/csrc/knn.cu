@@ -17,7 +17,8 @@
 // tau + err, and any member has d32 <= d64 + err <= tau + 2 err.
 //
 // Pilot threshold (N >= 32 N').  Before the stream, knn_pilot estimates each
-// location's N'-th distance from a stride sample of S design points: with
+// location's N'-th distance from a stride sample of S = min(32768, N / 16)
+// design points: with
 // lambda = S N'/N sample points expected inside it, the m-th smallest sample
 // distance, m = lambda + 4.5 sqrt(lambda) + 4, is above it except with
 // probability ~1e-5.  The stream starts with tau = that value instead of
@@ -30,6 +31,7 @@
 #include <cstdint>
 
 #include "common.cuh"
+#include "knn_common.cuh"
 #include "lagp_internal.h"
 
 namespace lagp {
@@ -37,10 +39,6 @@ namespace lagp {
 #define KNN_WARPS 8
 #define KNN_QW 4   // locations per warp
 
-struct __align__(8) KnnEntry {
-  float d;
-  int32_t idx;
-};
 
 // ---------------------------------------------------------------------------
 // Preparation: bounding box (exact min/max), centred FP32 copy of the design,
@@ -114,77 +112,6 @@ __global__ void design_to_f32(const double* __restrict__ X, int64_t N, int64_t N
   if ((threadIdx.x & 31) == 0) atomicMax(maxn2_bits, __float_as_uint(local_max));
 }
 
-// ---------------------------------------------------------------------------
-// Warp radix select: the k-th smallest (1-based) of cnt non-negative float
-// keys in e[0..cnt), returned as its bit pattern.  hist: 256 words of this
-// warp's shared memory.
-// ---------------------------------------------------------------------------
-__device__ uint32_t warp_select_kth(const KnnEntry* e, int cnt, int k, uint32_t* hist) {
-  const int lane = threadIdx.x & 31;
-  uint32_t prefix = 0, pmask = 0;
-  int kk = k;
-  for (int shift = 24; shift >= 0; shift -= 8) {
-    for (int b = lane; b < 256; b += 32) hist[b] = 0;
-    __syncwarp();
-    for (int i = lane; i < cnt; i += 32) {
-      uint32_t key = __float_as_uint(e[i].d);
-      if ((key & pmask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
-    }
-    __syncwarp();
-    // lane owns bins 8*lane .. 8*lane+7
-    uint32_t c[8], tot = 0;
-#pragma unroll
-    for (int b = 0; b < 8; ++b) { c[b] = hist[lane * 8 + b]; tot += c[b]; }
-    uint32_t incl = tot;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    uint32_t excl = incl - tot;
-    // the lane whose range holds the kk-th key finds the digit
-    int found = ((int)excl < kk && (int)incl >= kk);
-    uint32_t fmask = __ballot_sync(0xffffffffu, found);
-    int src = __ffs(fmask) - 1;
-    uint32_t digit = 0;
-    int kk_new = kk;
-    if (lane == src) {
-      uint32_t run = excl;
-#pragma unroll
-      for (int b = 0; b < 8; ++b) {
-        if ((int)(run + c[b]) >= kk) { digit = lane * 8 + b; kk_new = kk - (int)run; break; }
-        run += c[b];
-      }
-    }
-    digit = __shfl_sync(0xffffffffu, digit, src < 0 ? 0 : src);
-    kk = __shfl_sync(0xffffffffu, kk_new, src < 0 ? 0 : src);
-    prefix |= digit << shift;
-    pmask |= 255u << shift;
-    __syncwarp();
-  }
-  return prefix;
-}
-
-// Keep entries with d <= keep (stable, in place); returns the new count.
-__device__ int warp_compact(KnnEntry* e, int cnt, float keep) {
-  const int lane = threadIdx.x & 31;
-  int out = 0;
-  for (int base = 0; base < cnt; base += 32) {
-    int i = base + lane;
-    KnnEntry v;
-    bool ok = false;
-    if (i < cnt) { v = e[i]; ok = v.d <= keep; }
-    __syncwarp();
-    uint32_t m = __ballot_sync(0xffffffffu, ok);
-    if (ok) e[out + __popc(m & ((1u << lane) - 1u))] = v;
-    out += __popc(m);
-    __syncwarp();
-  }
-  return out;
-}
-
-// squared FP32 distance of a design row to the 4 locations of a warp, in the
-// stream's form |q|^2 + |x|^2 - 2 q.x
 template <int PP>
 __device__ __forceinline__ void knn_d4(const float (&qf)[KNN_QW][PP], const float (&nq)[KNN_QW],
                                        const float (&xv)[PP], float nxp, float (&d)[KNN_QW]) {
@@ -556,7 +483,9 @@ cudaError_t launch_prepare(const double* X, int64_t N, int p, int PP, int64_t Np
   prof_begin("design_to_f32", s);
   design_to_f32<<<1216, 256, 0, s>>>(X, N, Npad, p, PP, ws.center, ws.Xf, ws.nx, ws.maxn2);
   prof_end(s);
-  return cudaGetLastError();
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  return launch_design_to_tc(N, p, PP, Npad, ws, s);
 }
 
 cudaError_t launch_knn(const double* X, int64_t N, int p, int PP, int64_t Npad,
@@ -569,7 +498,7 @@ cudaError_t launch_knn(const double* X, int64_t N, int p, int PP, int64_t Npad,
   size_t sm = knn_smem_stream(PP);
   // pilot thresholds where the design is large against N'
   const bool pilot = N >= (int64_t)32 * nc_max;
-  const int64_t S = N / 16 < 16384 ? N / 16 : 16384;
+  const int64_t S = N / 16 < 32768 ? N / 16 : 32768;
   KnnEntry* kbuf = reinterpret_cast<KnnEntry*>(ws.knn_buf);
   cudaError_t err;
   switch (PP) {
@@ -584,12 +513,17 @@ cudaError_t launch_knn(const double* X, int64_t N, int p, int PP, int64_t Npad,
                                                    nc_max, nc_loc, cap, ws.knn_thr);         \
       prof_end(s);                                                                           \
     }                                                                                        \
-    prof_begin("knn_stream", s);                                                             \
-    knn_stream<V><<<grid, KNN_WARPS * 32, sm, s>>>(ws.Xf, ws.nx, N, ntiles, p, xref, M,      \
-                                                   ws.center, ws.maxn2, nc_max, nc_loc, cap, \
-                                                   kbuf, ws.knn_cnt, ws.status,              \
-                                                   pilot ? ws.knn_thr : nullptr, 0);         \
-    prof_end(s);                                                                             \
+    if (pilot) {                                                                             \
+      err = launch_knn_tc(Npad, p, xref, M, nc_max, nc_loc, cap, ws, s);                     \
+      if (err != cudaSuccess) return err;                                                    \
+    } else {                                                                                 \
+      prof_begin("knn_stream", s);                                                           \
+      knn_stream<V><<<grid, KNN_WARPS * 32, sm, s>>>(ws.Xf, ws.nx, N, ntiles, p, xref, M,    \
+                                                     ws.center, ws.maxn2, nc_max, nc_loc,    \
+                                                     cap, kbuf, ws.knn_cnt, ws.status,       \
+                                                     nullptr, 0);                            \
+      prof_end(s);                                                                           \
+    }                                                                                        \
     if (pilot) {                                                                             \
       prof_begin("knn_stream_redo", s);                                                      \
       knn_stream<V><<<grid, KNN_WARPS * 32, sm, s>>>(ws.Xf, ws.nx, N, ntiles, p, xref, M,    \

@@ -82,6 +82,7 @@ size_t layout_design(const Shape& sh, void* base, Workspace* ws) {
   w->center = static_cast<double*>(c.take(sizeof(double) * sh.p));
   w->Xf = static_cast<float*>(c.take(sizeof(float) * sh.Npad * sh.PP));
   w->nx = static_cast<float*>(c.take(sizeof(float) * sh.Npad));
+  w->Btc = static_cast<float*>(c.take(sizeof(float) * knn_tc_tile_floats(sh.Npad, sh.p)));
   return c.off;
 }
 

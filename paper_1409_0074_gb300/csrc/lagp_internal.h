@@ -19,6 +19,7 @@ struct Workspace {
   double* center;       // [p] box centre, origin of the FP32 coordinates
   float* Xf;            // [Npad][PP] centred FP32 design, PP = p rounded up to 4
   float* nx;            // [Npad] squared norms of Xf rows
+  float* Btc;           // design tiles of the tensor-core kNN filter (knn_tc.cu)
   void* knn_buf;        // [chunk][cap] (float d32, int32 index) candidate buffers
   int32_t* knn_cnt;     // [chunk] surviving buffer entries (-1: stream again)
   float* knn_thr;       // [chunk] pilot thresholds of the kNN stream
@@ -111,6 +112,11 @@ size_t knn_smem_stream(int PP);
 
 cudaError_t launch_prepare(const double* X, int64_t N, int p, int PP, int64_t Npad,
                            const Workspace& ws, cudaStream_t s);
+size_t knn_tc_tile_floats(int64_t Npad, int p);
+cudaError_t launch_design_to_tc(int64_t N, int p, int PP, int64_t Npad, const Workspace& ws,
+                                cudaStream_t s);
+cudaError_t launch_knn_tc(int64_t Npad, int p, const double* xref, int64_t M, int nc_max,
+                          const int32_t* nc_loc, int cap, const Workspace& ws, cudaStream_t s);
 cudaError_t launch_knn(const double* X, int64_t N, int p, int PP, int64_t Npad,
                        const double* xref, int64_t M, int nc_max, const int32_t* nc_loc,
                        int32_t* cand, const Workspace& ws, cudaStream_t s);

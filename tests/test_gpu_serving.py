@@ -84,10 +84,9 @@ def test_solo_mix_and_direct_results_are_identical(lagp, design):
 def test_admission_by_free_arena(lagp, design):
     import torch
     w, X, Y = design
-    probe = _ctx(lagp, design, 64 << 20)
     dbytes = lagp.load().laGP_ctx_design_bytes(w.N, w.p)
-    rb = probe.request_bytes(500, 50)
-    probe.close()
+    rb = lagp.load().laGP_ctx_request_bytes(w.N, w.p, 500, 50, N_CLOSE, NRAYS, lagp.LAGP_RAY,
+                                            lagp.LAGP_FP32_SCORE, 0)
     ctx = _ctx(lagp, design, dbytes + rb + 4096, slots=4)
     free, slots = ctx.capacity()
     assert free >= rb and slots == 4
