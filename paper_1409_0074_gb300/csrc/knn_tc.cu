@@ -22,11 +22,13 @@
 //               tcgen05.ld and compares them with its own threshold; a point
 //               that passes is appended to the location's buffer.
 // The threshold is the pilot's estimate of the N'-th distance plus 2 err and
-// stays fixed, so the buffer needs no compaction during the stream.  At the
-// end a location is valid when at least N' of its entries lie at or below the
-// pilot value and its buffer did not overflow; otherwise it is marked for the
-// streaming kernel's exact pass (threshold infinity).  knn_finalize then keeps
-// the entries within the N'-th smallest + 2 err for the exact ranking.
+// stays fixed, so the buffer needs no compaction during the stream.  Each
+// epilogue group appends to its own quarter of the location's buffer with a
+// counter in a register (no atomics in the stream).  At the end a location is
+// valid when at least N' of its entries lie at or below the pilot value and no
+// quarter overflowed; otherwise it is marked for the streaming kernel's exact
+// pass (threshold infinity).  knn_finalize joins the quarters and keeps the
+// entries within the N'-th smallest + 2 err for the exact ranking.
 //
 // err bounds |d_tc - d64| for the 3xTF32 contraction: operand splitting
 // (3 * 2^-22 |A_k B_k| per term), FP32 accumulation over 3K products
@@ -157,8 +159,8 @@ struct KtSmem {
   static constexpr int S_OFF = 2 * A_BYTES;
   static constexpr int KEEP_OFF = S_OFF + KT_STAGES * STAGE_BYTES;
   static constexpr int THR_OFF = KEEP_OFF + KT_M * 4;
-  static constexpr int CNT_OFF = THR_OFF + KT_M * 4;
-  static constexpr int BELOW_OFF = CNT_OFF + KT_M * 4;
+  static constexpr int CNT_OFF = THR_OFF + KT_M * 4;            // [KT_GROUPS][KT_M]
+  static constexpr int BELOW_OFF = CNT_OFF + KT_GROUPS * KT_M * 4;
   static constexpr int BAR_OFF = BELOW_OFF + KT_M * 4;
   static constexpr int MISC_OFF = BAR_OFF + (2 * KT_STAGES + 2 * KT_GROUPS) * 8;
   // + alignment slack; at least 120 KB so that one CTA (which takes all 512
@@ -172,7 +174,8 @@ __global__ void __launch_bounds__(KT_THREADS, 1)
 knn_tc(const float* __restrict__ Btiles, int64_t ntiles, int p, const double* __restrict__ xref,
        int64_t M, const double* __restrict__ center, const unsigned* __restrict__ maxn2_bits,
        int nc_max, const int32_t* __restrict__ nc_loc, int cap, const float* __restrict__ pilot,
-       KnnEntry* __restrict__ buf, int32_t* __restrict__ cnt_out, unsigned* __restrict__ status) {
+       KnnEntry* __restrict__ buf, int32_t* __restrict__ cnt_out, int32_t* __restrict__ seg_out,
+       unsigned* __restrict__ status) {
   using L = KtSmem<KA>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
@@ -209,7 +212,6 @@ knn_tc(const float* __restrict__ Btiles, int64_t ntiles, int p, const double* __
     // no pilot value: nothing is buffered and the exact pass takes the location
     thr_sm[c] = thr;
     keep_sm[c] = thr < inf ? __fadd_ru(thr, 2.f * kt_err(KA, r)) : -1.f;
-    cnt_sm[c] = 0;
     below_sm[c] = 0;
   }
   for (int e = tid; e < KT_M * KA; e += blockDim.x) {
@@ -316,7 +318,9 @@ knn_tc(const float* __restrict__ Btiles, int64_t ntiles, int p, const double* __
     const int64_t q = q0 + c;
     const uint32_t lane_base = taddr + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(g * KT_N);
     const float keep = keep_sm[c], thr = thr_sm[c];
-    KnnEntry* qb = buf + q * (int64_t)cap;
+    const int seg = cap / KT_GROUPS;                       // this group's quarter of the buffer
+    KnnEntry* qb = buf + q * (int64_t)cap + g * seg;
+    int mycnt = 0, mybelow = 0;
     for (int64_t t = g; t < ntiles; t += KT_GROUPS) {
       const bool ok = !*abort_v && mbar_wait(&tfull[g], (uint32_t)((t / KT_GROUPS) & 1));
       if (!__all_sync(0xffffffffu, ok)) *abort_v = 1;
@@ -341,24 +345,33 @@ knn_tc(const float* __restrict__ Btiles, int64_t ntiles, int p, const double* __
         for (int u = 0; u < 64; ++u) {
           const float d = __uint_as_float(v[u]);
           if (d <= keep) {
-            const int pos = atomicAdd(&cnt_sm[c], 1);
-            if (pos < cap) {
+            if (mycnt < seg) {
               KnnEntry e;
               e.d = fmaxf(d, 0.f);
               e.idx = pbase + c0 + u;
-              qb[pos] = e;
+              qb[mycnt] = e;
             }
-            if (d <= thr) atomicAdd(&below_sm[c], 1);
+            ++mycnt;
+            mybelow += (d <= thr) ? 1 : 0;
           }
         }
       }
     }
+    cnt_sm[g * KT_M + c] = mycnt;
+    atomicAdd(&below_sm[c], mybelow);
     kt_epi_barrier();
     if (g == 0 && q < M) {
       const int nc = nc_loc ? nc_loc[q] : nc_max;
-      const int n = cnt_sm[c];
+      int n = 0;
+      bool over = false;
+      for (int gg = 0; gg < KT_GROUPS; ++gg) {
+        const int k = cnt_sm[gg * KT_M + c];
+        over = over || k > seg;
+        seg_out[q * KT_GROUPS + gg] = k;
+        n += k;
+      }
       // valid: no overflow and at least N' entries at or below the pilot value
-      cnt_out[q] = (*abort_v) ? 0 : ((n <= cap && below_sm[c] >= nc && thr < inf) ? n : -1);
+      cnt_out[q] = (*abort_v) ? 0 : ((!over && below_sm[c] >= nc && thr < inf) ? n : -1);
     }
   }
   if (tid == 0 && *abort_v) atomicOr(status, LAGP_DEV_TIMEOUT);
@@ -377,7 +390,7 @@ __global__ void __launch_bounds__(256)
 knn_finalize(const double* __restrict__ xref, int64_t M, int p, int KA,
              const double* __restrict__ center, const unsigned* __restrict__ maxn2_bits,
              int nc_max, const int32_t* __restrict__ nc_loc, int cap, KnnEntry* __restrict__ buf,
-             int32_t* __restrict__ cnt) {
+             int32_t* __restrict__ cnt, const int32_t* __restrict__ seg_cnt) {
   __shared__ uint32_t hist[8][256];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t q = (int64_t)blockIdx.x * 8 + warp;
@@ -392,6 +405,23 @@ knn_finalize(const double* __restrict__ xref, int64_t M, int p, int KA,
   }
   const float r = sqrtf(__uint_as_float(*maxn2_bits)) * 1.0001f + sqrtf(qn) * 1.0001f;
   KnnEntry* e = buf + q * (int64_t)cap;
+  // join the quarters: quarter g (count k_g) moves down to the end of the
+  // entries before it; reading a chunk before writing it keeps the forward
+  // copy safe (the destination never passes the source)
+  const int seg = cap / KT_GROUPS;
+  int at = seg_cnt[q * KT_GROUPS];
+  for (int g = 1; g < KT_GROUPS; ++g) {
+    const int k = seg_cnt[q * KT_GROUPS + g];
+    for (int b0 = 0; b0 < k; b0 += 32) {
+      KnnEntry v;
+      const bool in = b0 + lane < k;
+      if (in) v = e[g * seg + b0 + lane];
+      __syncwarp();
+      if (in) e[at + b0 + lane] = v;
+      __syncwarp();
+    }
+    at += k;
+  }
   const uint32_t kb = warp_select_kth(e, c, nc, hist[warp]);
   const int nn = warp_compact(e, c, __fadd_ru(__uint_as_float(kb), 2.f * kt_err(KA, r)));
   if (lane == 0) cnt[q] = nn;
@@ -423,7 +453,7 @@ cudaError_t launch_knn_tc(int64_t Npad, int p, const double* xref, int64_t M, in
     prof_begin("knn_tc", s);                                                                    \
     knn_tc<V><<<grid, KT_THREADS, sm, s>>>(ws.Btc, ntiles, p, xref, M, ws.center, ws.maxn2,     \
                                            nc_max, nc_loc, cap, ws.knn_thr, kbuf, ws.knn_cnt,   \
-                                           ws.status);                                          \
+                                           ws.knn_seg, ws.status);                              \
     prof_end(s);                                                                                \
     break;                                                                                      \
   }
@@ -436,7 +466,8 @@ cudaError_t launch_knn_tc(int64_t Npad, int p, const double* xref, int64_t M, in
   }
   prof_begin("knn_finalize", s);
   knn_finalize<<<(unsigned)((M + 7) / 8), 256, 0, s>>>(xref, M, p, KA, ws.center, ws.maxn2,
-                                                       nc_max, nc_loc, cap, kbuf, ws.knn_cnt);
+                                                       nc_max, nc_loc, cap, kbuf, ws.knn_cnt,
+                                                       ws.knn_seg);
   prof_end(s);
   return cudaGetLastError();
 }

@@ -44,6 +44,7 @@ size_t layout_request(const Shape& sh, void* base, Workspace* ws) {
   w->knn_buf = c.take((size_t)8 * ch * knn_cap(sh.nc_max));
   w->knn_cnt = static_cast<int32_t*>(c.take(sizeof(int32_t) * ch));
   w->knn_thr = static_cast<float*>(c.take(sizeof(float) * ch));
+  w->knn_seg = static_cast<int32_t*>(c.take(sizeof(int32_t) * 4 * ch));
   w->cand = static_cast<int32_t*>(c.take(sizeof(int32_t) * ch * sh.nc_max));
   size_t s64 = 0, s32 = 0;
   if (sh.precision == LAGP_FP64) {

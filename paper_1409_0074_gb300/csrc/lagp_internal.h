@@ -23,6 +23,7 @@ struct Workspace {
   void* knn_buf;        // [chunk][cap] (float d32, int32 index) candidate buffers
   int32_t* knn_cnt;     // [chunk] surviving buffer entries (-1: stream again)
   float* knn_thr;       // [chunk] pilot thresholds of the kNN stream
+  int32_t* knn_seg;     // [chunk][4] entries per buffer quarter (tensor-core filter)
   int32_t* cand;        // [chunk][nc_max] candidate design indices, nearest first
   double* state64;      // FP64 state: FP64 form, exhaustive: [chunk][nc_max][n_max]
                         // correlation cache; FP32 form: per slot, L^{-1} and its vectors
