@@ -127,6 +127,34 @@ __device__ __forceinline__ double corr64_fast(const double* a, const double* b, 
   return exp_neg_fma((d0 + d1) * neg_inv_theta);
 }
 
+// sum_{k=0..len-1} u[k] * v[k] in binary64 with eight independent accumulators,
+// so that eight loads of u (global memory) are in flight at a time and no
+// single FMA chain sets the pace (GB300's FP64 and L2 latencies).
+__device__ __forceinline__ double dot64_ilp8(const double* u, const double* v, int len) {
+  double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  int k = 0;
+  for (; k + 7 < len; k += 8) {
+#pragma unroll
+    for (int t = 0; t < 8; ++t) a[t] = fma(u[k + t], v[k + t], a[t]);
+  }
+  for (; k < len; ++k) a[0] = fma(u[k], v[k], a[0]);
+  return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+}
+
+// sum_{i=k..j-1} u[i] * M[i * ld + k] (a column of a row-major matrix) in
+// binary64, eight accumulators as above
+__device__ __forceinline__ double coldot64_ilp8(const double* u, const double* M, int64_t ld, int k,
+                                                int j) {
+  double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  int i = k;
+  for (; i + 7 < j; i += 8) {
+#pragma unroll
+    for (int t = 0; t < 8; ++t) a[t] = fma(u[i + t], M[(int64_t)(i + t) * ld + k], a[t]);
+  }
+  for (; i < j; ++i) a[0] = fma(u[i], M[(int64_t)i * ld + k], a[0]);
+  return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+}
+
 // sum_{k=0..len-1} u[k] * v[k] in binary64 with four independent accumulators
 // (GB300's FP64 latency makes a single FMA chain the critical path).
 __device__ __forceinline__ double dot64_ilp(const double* u, const double* v, int len) {

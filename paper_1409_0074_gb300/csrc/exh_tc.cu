@@ -57,6 +57,7 @@ struct XtParams {
   int32_t* nevals;
   double* Linv;          // [slots][n_max][n_max]
   float* Kc;             // [slots][ceil(nc_max / 128)] tiles of 2 x 128 x XT_KMAX floats
+  float* crow;           // [slots][nc_max][PP] the location's candidates' FP32 rows
   unsigned* status;
   unsigned* queue;       // work counter (zero at launch)
   const int32_t* order;  // item -> location, or null
@@ -107,6 +108,22 @@ __device__ __forceinline__ void xld16(uint32_t addr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// block sums of two values at once (one pass of shuffles and barriers)
+__device__ __forceinline__ void xsum2(double& a, double& b, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  __syncthreads();
+  if (lane == 0) { red[2 * warp] = a; red[2 * warp + 1] = b; }
+  __syncthreads();
+  double ta = 0.0, tb = 0.0;
+  for (int w = 0; w < XT_THREADS / 32; ++w) { ta += red[2 * w]; tb += red[2 * w + 1]; }
+  a = ta;
+  b = tb;
+}
+
 __device__ __forceinline__ double xsum(double v, double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -126,7 +143,7 @@ struct XtSmem {
   static constexpr int END = A_OFF + 2 * A_BYTES;         // 96 KB
 };
 
-__global__ void __launch_bounds__(XT_THREADS) exh_tc_kernel(XtParams P) {
+__global__ void __launch_bounds__(XT_THREADS, 2) exh_tc_kernel(XtParams P) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -147,7 +164,8 @@ __global__ void __launch_bounds__(XT_THREADS) exh_tc_kernel(XtParams P) {
   double* zy = z + XT_KMAX;
   double* kv = zy + XT_KMAX;
   double* lv = kv + XT_KMAX;
-  double* red = lv + XT_KMAX;                                         // [8]
+  double* ys = lv + XT_KMAX;                                          // [XT_KMAX] y of S
+  double* red = ys + XT_KMAX;                                         // [8]
   float* fred = reinterpret_cast<float*>(red + 8);                    // [8]
   int* ired = reinterpret_cast<int*>(fred + 8);                       // [8]
   int* sel = ired + 8;                                                // [XT_KMAX]
@@ -178,6 +196,7 @@ __global__ void __launch_bounds__(XT_THREADS) exh_tc_kernel(XtParams P) {
   double* Lg = P.Linv + (int64_t)blockIdx.x * ld * ld;
   const int ntc = (nc_max + 127) / 128;
   float* Kc = P.Kc + (int64_t)blockIdx.x * ntc * 2 * XT_TILE_FLOATS;
+  float* crow = P.crow + (int64_t)blockIdx.x * nc_max * PP;
   for (int64_t i = tid; i < (int64_t)ntc * 2 * XT_TILE_FLOATS / 4; i += XT_THREADS)
     reinterpret_cast<float4*>(Kc)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -203,10 +222,16 @@ __global__ void __launch_bounds__(XT_THREADS) exh_tc_kernel(XtParams P) {
     const double* xq = P.xref + loc * p;
 
     for (int i = tid; i < 2 * XtSmem::B_BYTES / 4; i += XT_THREADS) Bhi[i] = 0.f;
+    // the candidates' FP32 rows, gathered once into the slot in rank order (the
+    // correlation column of every step then reads them contiguously), and K(c_r, x)
     for (int r = tid; r < nc; r += XT_THREADS) {
       used[r] = 0;
       const float* c = P.Xf + (int64_t)cl[r] * PP;
       float d = 0.f;
+      for (int k = 0; k < PP; k += 4) {
+        const float4 v4 = *reinterpret_cast<const float4*>(c + k);
+        *reinterpret_cast<float4*>(crow + (int64_t)r * PP + k) = v4;
+      }
       for (int k = 0; k < p; ++k) {
         const float t = c[k] - (float)(xq[k] - P.center[k]);
         d = fmaf(t, t, d);
@@ -225,12 +250,22 @@ __global__ void __launch_bounds__(XT_THREADS) exh_tc_kernel(XtParams P) {
       const double* c = P.X + (int64_t)cl[rr] * p;
       if (tid < p) S64[j * p + tid] = c[tid];
       __syncthreads();
-      for (int i = tid; i < j; i += XT_THREADS) kv[i] = corr64_fast(S64 + i * p, S64 + j * p, p, nit64);
+      // correlations of the new point with the design (and with x, on the idle thread j)
+      for (int i = tid; i <= j; i += XT_THREADS) {
+        if (i < j) {
+          kv[i] = corr64_fast(S64 + i * p, S64 + j * p, p, nit64);
+        } else {
+          kx[j] = corr64_fast(S64 + j * p, xq, p, nit64);
+          ys[j] = P.Y[cl[rr]];
+          sel[j] = rr;
+          used[rr] = 1;
+        }
+      }
       __syncthreads();
       double vv = 0.0;
       for (int i = tid; i < j; i += XT_THREADS) {
         const double* Li = Lg + (int64_t)i * ld;
-        const double acc = dot64_ilp(Li, kv, i + 1);
+        const double acc = dot64_ilp8(Li, kv, i + 1);
         lv[i] = acc;
         vv = fma(acc, acc, vv);
       }
@@ -240,37 +275,21 @@ __global__ void __launch_bounds__(XT_THREADS) exh_tc_kernel(XtParams P) {
       const double inv_d = 1.0 / sqrt(v);
       for (int k = tid; k <= j; k += XT_THREADS) {
         double rk = inv_d;
-        if (k < j) {
-          double a0 = 0.0, a1 = 0.0;
-          int i = k;
-          for (; i + 1 < j; i += 2) {
-            a0 = fma(lv[i], Lg[(int64_t)i * ld + k], a0);
-            a1 = fma(lv[i + 1], Lg[(int64_t)(i + 1) * ld + k], a1);
-          }
-          if (i < j) a0 = fma(lv[i], Lg[(int64_t)i * ld + k], a0);
-          const double acc = a0 + a1;
-          rk = -acc * inv_d;
-        }
+        if (k < j) rk = -coldot64_ilp8(lv, Lg, ld, k, j) * inv_d;
         Lg[(int64_t)j * ld + k] = rk;
         const float h = xtf32((float)rk);
         const uint32_t off = xcanon(j, k) >> 2;
         Bhi[off] = h;
         Blo[off] = xtf32((float)(rk - (double)h));
       }
-      if (tid == 0) {
-        kx[j] = corr64_fast(S64 + j * p, xq, p, nit64);
-        sel[j] = rr;
-        used[rr] = 1;
-      }
       __syncthreads();
       double zz = 0.0, zyy = 0.0;
       for (int k = tid; k <= j; k += XT_THREADS) {
         const double rk = Lg[(int64_t)j * ld + k];
         zz = fma(rk, kx[k], zz);
-        zyy = fma(rk, P.Y[cl[sel[k]]], zyy);
+        zyy = fma(rk, ys[k], zyy);
       }
-      zz = xsum(zz, red);
-      zyy = xsum(zyy, red);
+      xsum2(zz, zyy, red);
       if (tid == 0) {
         z[j] = zz;
         zy[j] = zyy;
@@ -278,9 +297,9 @@ __global__ void __launch_bounds__(XT_THREADS) exh_tc_kernel(XtParams P) {
       }
       // correlation cache column j: K(c_r, S_j) for every candidate, as A operand
       // (TF32 hi / lo) of its tile; then visible to the bulk copies
-      const float* sj = P.Xf + (int64_t)cl[rr] * PP;
+      const float* sj = crow + (int64_t)rr * PP;
       for (int q = tid; q < nc; q += XT_THREADS) {
-        const float kv = __expf(sqdist_row32(P.Xf + (int64_t)cl[q] * PP, sj, PP) * nit);
+        const float kv = __expf(sqdist_row32(crow + (int64_t)q * PP, sj, PP) * nit);
         const float h = xtf32(kv);
         float* tile = Kc + (int64_t)(q >> 7) * 2 * XT_TILE_FLOATS;
         const uint32_t off = xcanon(q & 127, j) >> 2;
@@ -463,8 +482,9 @@ cudaError_t launch_exh_tc(const DesignArgs& a, cudaStream_t s) {
   P.s2 = a.s2; P.selected = a.selected; P.tie_gap = a.tie_gap; P.nevals = a.nevals;
   P.Linv = a.ws->state64; P.Kc = a.ws->state32; P.status = a.ws->status;
   P.queue = a.ws->queue + 1; P.order = a.order; P.count = a.count;
+  P.crow = a.ws->crow;
   const size_t small = (size_t)((a.nc_max + 3) & ~3) * 4 + XT_KMAX * 4 + (size_t)XT_KMAX * a.p * 8 +
-                       5 * XT_KMAX * 8 + 8 * 8 + 8 * 4 + 8 * 4 + XT_KMAX * 4 + a.nc_max + 96;
+                       6 * XT_KMAX * 8 + 8 * 8 + 8 * 4 + 8 * 4 + XT_KMAX * 4 + a.nc_max + 96;
   const size_t sm = 1024 + XtSmem::END + small;
   cudaError_t err =
       cudaFuncSetAttribute(exh_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -62,6 +62,9 @@ size_t layout_request(const Shape& sh, void* base, Workspace* ws) {
   }
   w->state64 = static_cast<double*>(c.take(s64));
   w->state32 = static_cast<float*>(c.take(s32));
+  const bool fp32_exh = sh.precision != LAGP_FP64 && sh.search == LAGP_EXHAUSTIVE;
+  w->crow = static_cast<float*>(
+      c.take(fp32_exh ? sizeof(float) * exh_slots(ch) * sh.nc_max * sh.PP : 0));
   w->queue = static_cast<unsigned*>(c.take(4 * sizeof(unsigned)));
   w->order = static_cast<int32_t*>(c.take(sizeof(int32_t) * 2 * ch));
   w->order_hist = static_cast<unsigned*>(c.take(512 * sizeof(unsigned)));

@@ -28,6 +28,7 @@ struct Workspace {
   double* state64;      // FP64 state: FP64 form, exhaustive: [chunk][nc_max][n_max]
                         // correlation cache; FP32 form: per slot, L^{-1} and its vectors
   float* state32;       // FP32 form, exhaustive: [slots][n_max][nc_max] correlation cache
+  float* crow;          // FP32 form, exhaustive: [CTA slots][nc_max][PP] candidate rows
   unsigned* queue;      // [4] work counters of the persistent kernels
   int32_t* order;       // [2][chunk] work order (largest local designs first), two parts
   unsigned* order_hist; // [2][256] cost-bucket counts, then offsets
