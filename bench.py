@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--M", type=int, default=100_000)
     ap.add_argument("--N", type=int, default=1_000_000)
     ap.add_argument("--search", default="ray", choices=["ray", "exhaustive"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_tc", "fp64"])
     ap.add_argument("--no-extras", action="store_true", help="skip the other search/precision forms")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle locations (0: 32 per core)")
@@ -453,7 +453,7 @@ def base_line(args, world, value, ms, w):
             "config": {"workload": w.name, "N": w.N, "p": w.p, "M": w.M, "n0": w.n0, "n": w.n,
                        "N_close": w.nc, "theta": w.theta, "g": w.g, "search": args.search,
                        "nrays": w.nrays,
-                       "precision": "fp32 scoring, fp64 update" if args.precision == "fp32"
+                       "precision": "fp32 scoring, fp64 update" if args.precision != "fp64"
                        else "fp64", "l2": "flushed: 256 MB written before every step",
                        "parallelism": "locations sharded over %d rank(s)" % world}}
 
@@ -487,7 +487,7 @@ def main():
     r = run_ours(args, rank, world)
     w = r["w"]
     line = base_line(args, world, r["value"], r["ms"], w)
-    line.update({"dtype": "f32/f64" if args.precision == "fp32" else "f64",
+    line.update({"dtype": "f32/f64" if args.precision != "fp64" else "f64",
                  "roofline": r["roofline"], "clocks": r["clocks"],
                  "gpu_launches": r["gpu_launches"], "kernels": r["kernels"],
                  "rmse": r["rmse"], "ray_evals_per_step": r["evals_per_step"],
@@ -497,6 +497,8 @@ def main():
         if not args.no_extras:
             ex = {}
             ex["exhaustive_fp32"] = run_extra(args, w, r["tensors"], "exhaustive", "fp32", w.M)
+            ex["exhaustive_fp32_tc"] = run_extra(args, w, r["tensors"], "exhaustive", "fp32_tc",
+                                                 w.M)
             ex["ray_fp64"] = run_extra(args, w, r["tensors"], "ray", "fp64", min(w.M, 4000))
             ex["exhaustive_fp64"] = run_extra(args, w, r["tensors"], "exhaustive", "fp64",
                                               min(w.M, 1000), steps=1)

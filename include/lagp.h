@@ -52,9 +52,18 @@ extern "C" {
  *   partitioned-inverse update, in a fixed operation order (the parity form).
  * LAGP_FP32_SCORE: candidate and ray scoring in FP32 through the inverse
  *   Cholesky factor L_j^{-1} (k^T K^{-1} k = |L^{-1} k|^2); the factor update,
- *   its Schur complement and the predictive equations stay in binary64. */
+ *   its Schur complement and the predictive equations stay in binary64.
+ *   Exhaustive search keeps every candidate's running |L^{-1} k|^2 and
+ *   (L^{-1} k) . (L^{-1} k(x)), extended by one term per step (the factor
+ *   only gains a row), on the FP32 CUDA cores.
+ * LAGP_FP32_SCORE_TC: as LAGP_FP32_SCORE, but exhaustive search forms all of
+ *   W = Kc L_j^{-T} at every step as a dense contraction on the tensor cores
+ *   (3xTF32 split products, FP32 accumulation) for local designs up to 64
+ *   points (larger ones as LAGP_FP32_SCORE).  Same method and tolerances,
+ *   other rounding; ray search is the same as LAGP_FP32_SCORE. */
 #define LAGP_FP64 0
 #define LAGP_FP32_SCORE 1
+#define LAGP_FP32_SCORE_TC 2
 
 /* Return codes. */
 #define LAGP_OK 0
@@ -94,7 +103,7 @@ size_t laGP_workspace_bytes(int64_t N, int p, int64_t M, int n, int N_close, int
  *   search    LAGP_EXHAUSTIVE or LAGP_RAY
  *   nrays     rays per step for LAGP_RAY (<= 0 selects p; at most 16 and at
  *             most N_close - n); ignored for LAGP_EXHAUSTIVE
- *   precision LAGP_FP64 or LAGP_FP32_SCORE
+ *   precision LAGP_FP64, LAGP_FP32_SCORE or LAGP_FP32_SCORE_TC
  *   n_loc     device [M] int32 or NULL: per-location final size (each in
  *             [n0, n]); NULL gives every location n
  *   nclose_loc device [M] int32 or NULL: per-location N_close (each in

@@ -1,6 +1,7 @@
 // design_fp32.cu -- exhaustive greedy local design with FP32 candidate scoring
-// and an FP64 factor update, one CTA per predictive location (the ray search
-// of this form is in ray32.cu).
+// and an FP64 factor update, one CTA per predictive location, for designs
+// larger than the tensor-core scorer takes (the ray search of this form is in
+// ray32.cu).
 //
 // Scoring form.  With K_j = L_j L_j^T (Cholesky) the ALC integrand of Eq. alc
 // (sign reading as in the FP64 path) becomes
@@ -19,6 +20,13 @@
 // so one new row per step, O(j^2).  z and L^{-1} y grow by one entry per step
 // and the predictive equations (Eq. predgp, preds2) follow as
 //     mu = z . (L^{-1} y),  psi = |L^{-1} y|^2,  sigma^2 = psi (1 + g - |z|^2) / n.
+//
+// Incremental scores.  Because the inverse factor only gains a row, every
+// candidate's w (and z) only gains an entry per step: w_cj = row_j . K(S, c).
+// Each CTA keeps |w_c|^2 and w_c . z as running sums per candidate, so a step
+// costs O(N' j) instead of the O(N' j^2) of re-forming every w, and a full
+// design O(N' n^2) instead of O(N' n^3); the sums see the same FP32 operations
+// in the same order as a from-scratch evaluation would.
 // Scoring coordinates are FP32 and centred on the design's bounding box.
 #include <cstdint>
 
@@ -29,8 +37,6 @@ namespace lagp {
 
 #define D32_THREADS 256
 #define D32_WARPS (D32_THREADS / 32)
-// candidates scored per pass of the exhaustive search (shared-memory tile rows)
-__host__ __device__ __forceinline__ int exh_pass(int n_max) { return n_max <= 64 ? 256 : 128; }
 
 struct D32Params {
   const double* X;
@@ -45,9 +51,6 @@ struct D32Params {
   int n0, n_max;
   const int32_t* n_loc;
   double theta, g;
-  int R;
-  const double* lo;
-  const double* hi;
   const double* center;
   double* mean;
   double* s2;
@@ -67,15 +70,9 @@ struct L32 {
   float* zf;       // [n_max]
   float* Sf;       // [n_max][PP] centred FP32 selected coordinates
   float* xf;       // [PP]
-  float* lof;      // [PP]
-  float* hif;      // [PP]
-  float* kzf;      // [WARPS][n_max]  (exhaustive: [exh_pass][ldf] tile)
-  float* rz;       // [WARPS][PP]
-  float* rA;       // [R][PP]
-  float* rE;       // [R][PP]
-  float* ralc;     // [R]
-  float* rs;       // [R]
-  float* xs;       // [PP]
+  float* vs;       // [nc_max] running |w_c|^2 of every candidate
+  float* ns;       // [nc_max] running w_c . z
+  float* kxc;      // [nc_max] K(c, x)
   float* red;      // [WARPS*4]
   double* S64;     // [n_max][p]
   double* xq;      // [p]
@@ -85,10 +82,7 @@ struct L32 {
   double* zy;      // [n_max]
   double* kx;      // [n_max]
   double* dred;    // [WARPS*4]
-  double* dscal;   // [4]
   int* sel;        // [n_max]
-  int* starts;     // [R]
-  int* rnev;       // [R]
   int* ired;       // [WARPS*2]
   unsigned char* used;
   int j, ldf;
@@ -103,16 +97,41 @@ __device__ __forceinline__ double warp_sumd(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
-// block sum of up to 2 doubles; all threads receive the result
-__device__ void block_sum2(double& a, double& b, double* scratch) {
+// Sum over the block of FP64 terms held only by threads below `active`, to
+// thread 0 (the other threads' a, b are left as their warp sums or unchanged).
+// Only the warps holding terms shuffle, and thread 0 adds the warp totals in
+// warp order, so the result is bit-identical to a full block sum (the idle
+// warps' totals are exact zeros) at a fraction of its FP64 instructions,
+// which are scarce on this part.  Every thread must call it.
+__device__ __forceinline__ void sum_to_thread0(double& a, double& b, int active, double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  a = warp_sumd(a);
-  b = warp_sumd(b);
-  if (lane == 0) { scratch[2 * warp] = a; scratch[2 * warp + 1] = b; }
+  const int aw = min((active + 31) >> 5, D32_WARPS);
+  if (warp < aw) {
+    a = warp_sumd(a);
+    b = warp_sumd(b);
+    if (lane == 0) { red[2 * warp] = a; red[2 * warp + 1] = b; }
+  }
   __syncthreads();
-  a = 0.0; b = 0.0;
-  for (int w = 0; w < D32_WARPS; ++w) { a += scratch[2 * w]; b += scratch[2 * w + 1]; }
+  if (threadIdx.x == 0) {
+    double ta = 0.0, tb = 0.0;
+    for (int w = 0; w < aw; ++w) { ta += red[2 * w]; tb += red[2 * w + 1]; }
+    a = ta;
+    b = tb;
+  }
+}
+__device__ __forceinline__ void sum_to_thread0(double& a, int active, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int aw = min((active + 31) >> 5, D32_WARPS);
+  if (warp < aw) {
+    a = warp_sumd(a);
+    if (lane == 0) red[warp] = a;
+  }
   __syncthreads();
+  if (threadIdx.x == 0) {
+    double ta = 0.0;
+    for (int w = 0; w < aw; ++w) ta += red[w];
+    a = ta;
+  }
 }
 
 // best (value, index) over the block: larger value wins, ties to the lower index
@@ -150,8 +169,8 @@ __device__ __forceinline__ const float* cand_f(const D32Params& P, const int32_t
   return P.Xf + (int64_t)cl[r] * P.PP;
 }
 
-// Append candidate rank r: FP64 factor row, z, L^{-1}y, FP32 copies.
-template <int SEARCH>
+// Append candidate rank r: FP64 factor row, z, L^{-1}y, FP32 copies, the
+// correlation-cache row K(S_j, c) and entry j of every unselected candidate's w.
 __device__ bool add_point32(const D32Params& P, L32& L, const int32_t* cl, int nc, int r,
                             double* Lg, float* Kc_loc) {
   const int tid = threadIdx.x, p = P.p, j = L.j, ld = P.n_max;
@@ -160,19 +179,29 @@ __device__ bool add_point32(const D32Params& P, L32& L, const int32_t* cl, int n
   if (tid < P.PP) L.Sf[j * P.PP + tid] = cand_f(P, cl, r)[tid];
   __syncthreads();
   const double nit64 = -1.0 / P.theta;
-  for (int i = tid; i < j; i += blockDim.x)
-    L.kvec[i] = corr64_fast(L.S64 + i * p, L.S64 + j * p, p, nit64);
+  // correlations of the new point with the design, and with x (thread j)
+  for (int i = tid; i <= j; i += blockDim.x) {
+    if (i < j) L.kvec[i] = corr64_fast(L.S64 + i * p, L.S64 + j * p, p, nit64);
+    else L.kx[j] = corr64_fast(L.S64 + j * p, L.xq, p, nit64);
+  }
   __syncthreads();
-  double vv = 0.0, dummy = 0.0;
+  // l = L_j^{-1} k_j(x_new); thread 0 forms the pivot v = 1 + g - |l|^2, 1/sqrt(v)
+  double vv = 0.0;
   for (int i = tid; i < j; i += blockDim.x) {
     const double acc = dot64_ilp(Lg + (int64_t)i * ld, L.kvec, i + 1);
     L.l[i] = acc;
     vv = fma(acc, acc, vv);
   }
-  block_sum2(vv, dummy, L.dred);
-  const double v = (1.0 + P.g) - vv;
-  if (!(v > 0.0)) return false;
-  const double inv_d = 1.0 / sqrt(v);
+  sum_to_thread0(vv, j, L.dred);
+  double* piv = L.dred + 2 * D32_WARPS;
+  if (tid == 0) {
+    const double v = (1.0 + P.g) - vv;
+    piv[0] = v;
+    piv[1] = v > 0.0 ? 1.0 / sqrt(v) : 0.0;
+  }
+  __syncthreads();
+  if (!(piv[0] > 0.0)) return false;
+  const double inv_d = piv[1];
   for (int k = tid; k < j; k += blockDim.x) {
     double a0 = 0.0, a1 = 0.0;
     int i = k;
@@ -188,7 +217,6 @@ __device__ bool add_point32(const D32Params& P, L32& L, const int32_t* cl, int n
   if (tid == 0) {
     Lg[(int64_t)j * ld + j] = inv_d;
     L.Lf[j * L.ldf + j] = (float)inv_d;
-    L.kx[j] = corr64_fast(L.S64 + j * p, L.xq, p, nit64);
     L.sel[j] = r;
     L.used[r] = 1;
   }
@@ -200,17 +228,38 @@ __device__ bool add_point32(const D32Params& P, L32& L, const int32_t* cl, int n
     zz = fma(rk, L.kx[k], zz);
     zyy = fma(rk, P.Y[cl[L.sel[k]]], zyy);
   }
-  block_sum2(zz, zyy, L.dred);
+  sum_to_thread0(zz, zyy, j + 1, L.dred);
   if (tid == 0) {
     L.z[j] = zz;
     L.zy[j] = zyy;
     L.zf[j] = (float)zz;
   }
-  if (SEARCH == 0) {
-    float* row = Kc_loc + (int64_t)j * P.nc_max;
-    const float* sj = L.Sf + j * P.PP;
-    for (int q = tid; q < nc; q += blockDim.x)
-      row[q] = __expf(sqdist_row32(cand_f(P, cl, q), sj, P.PP) * L.neg_inv_theta);
+  __syncthreads();
+  // Row j of L^{-1} is final once written, so w_c = L^{-1} k_j(c) only gains
+  // the entry w_cj = row_j . K(S_{0..j}, c); |w_c|^2 and w_c . z are running
+  // sums in the order i = 0, 1, ..., the same FP32 operations a from-scratch
+  // evaluation at every step would perform.  Thread q owns candidates
+  // q, q + blockDim, ..., so the cache row it writes is the one it reads back.
+  const int64_t ldc = P.nc_max;
+  float* row = Kc_loc + (int64_t)j * ldc;
+  const float* sj = L.Sf + j * P.PP;
+  const float* Lfj = L.Lf + j * L.ldf;
+  const float zj = L.zf[j];
+  for (int q = tid; q < nc; q += blockDim.x) {
+    row[q] = __expf(sqdist_row32(cand_f(P, cl, q), sj, P.PP) * L.neg_inv_theta);
+    if (L.used[q]) continue;
+    const float* kc = Kc_loc + q;
+    float a0 = 0.f, a1 = 0.f;
+    int k = 0;
+#pragma unroll 4
+    for (; k + 1 <= j; k += 2) {
+      a0 = fmaf(Lfj[k], kc[k * ldc], a0);
+      a1 = fmaf(Lfj[k + 1], kc[(k + 1) * ldc], a1);
+    }
+    if (k <= j) a0 = fmaf(Lfj[k], kc[k * ldc], a0);
+    const float w = a0 + a1;
+    L.vs[q] = fmaf(w, w, L.vs[q]);
+    L.ns[q] = fmaf(w, zj, L.ns[q]);
   }
   __syncthreads();
   L.j = j + 1;
@@ -218,56 +267,30 @@ __device__ bool add_point32(const D32Params& P, L32& L, const int32_t* cl, int n
 }
 
 // ----- exhaustive search, CUDA-core FP32 scoring ---------------------------------
-__device__ int search_exh32(const D32Params& P, L32& L, const int32_t* cl, int nc,
-                            const float* Kc_loc, double* gap_out) {
-  const int tid = threadIdx.x, j = L.j, ldt = L.ldf;
-  float* T = L.kzf;   // [pass][ldt]
-  const int pass = exh_pass(P.n_max);
+// ALC_c = (w_c . z - K(c, x))^2 / ((1 + g) - |w_c|^2) from the running sums;
+// the largest score wins, ties to the lower candidate rank.
+__device__ int search_exh32(const L32& L, int nc, double* gap_out) {
   VI best; best.v = -1.f; best.v2 = -1.f; best.i = -1;
-  for (int base = 0; base < nc; base += pass) {
-    const int cnt = min(pass, nc - base);
-    // stage the pass's correlation rows, transposed: T[r][i] = K(S_i, c_r)
-    for (int e = tid; e < j * pass; e += blockDim.x) {
-      const int i = e / pass, rr = e - i * pass;
-      if (rr < cnt) T[rr * ldt + i] = Kc_loc[(int64_t)i * P.nc_max + base + rr];
-    }
-    __syncthreads();
-    const int r = base + tid;
-    if (tid < cnt && !L.used[r]) {
-      const float* kc = T + tid * ldt;
-      float vs = 0.f, ns = 0.f;
-      for (int i = 0; i < j; ++i) {
-        const float* Li = L.Lf + i * ldt;
-        float a0 = 0.f, a1 = 0.f;
-        int k = 0;
-        for (; k + 1 <= i; k += 2) { a0 = fmaf(Li[k], kc[k], a0); a1 = fmaf(Li[k + 1], kc[k + 1], a1); }
-        if (k <= i) a0 = fmaf(Li[k], kc[k], a0);
-        const float w = a0 + a1;
-        vs = fmaf(w, w, vs);
-        ns = fmaf(w, L.zf[i], ns);
-      }
-      const float d = sqdist_row32(cand_f(P, cl, r), L.xf, P.PP);
-      const float v = L.onepg - vs;
-      const float num = ns - __expf(d * L.neg_inv_theta);
-      const float alc = v > 0.f ? num * num / v : 0.f;
-      if (alc > best.v) { best.v2 = best.v; best.v = alc; best.i = r; }
-      else if (alc > best.v2) best.v2 = alc;
-    }
-    __syncthreads();
+  for (int r = threadIdx.x; r < nc; r += blockDim.x) {
+    if (L.used[r]) continue;
+    const float v = L.onepg - L.vs[r];
+    const float num = L.ns[r] - L.kxc[r];
+    const float alc = v > 0.f ? num * num / v : 0.f;
+    if (alc > best.v) { best.v2 = best.v; best.v = alc; best.i = r; }
+    else if (alc > best.v2) best.v2 = alc;
   }
   VI b = block_best(best, L.red, L.ired);
   *gap_out = (b.v > 0.f && b.v2 >= 0.f) ? (double)((b.v - b.v2) / b.v) : 0.0;
   return b.i;
 }
 
-template <int SEARCH>
 __global__ void __launch_bounds__(D32_THREADS) design32(D32Params P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned s_item;
-  const int tid = threadIdx.x, p = P.p, PP = P.PP, ld = P.n_max, R = P.R;
+  const int tid = threadIdx.x, p = P.p, PP = P.PP, ld = P.n_max;
   // scratch of this CTA slot
   double* Lg = P.Linv + (int64_t)blockIdx.x * ld * ld;
-  float* Kc_loc = (SEARCH == 0) ? P.Kc + (int64_t)blockIdx.x * ld * P.nc_max : nullptr;
+  float* Kc_loc = P.Kc + (int64_t)blockIdx.x * ld * P.nc_max;
 
   L32 L;
   L.ldf = ld | 1;
@@ -280,26 +303,17 @@ __global__ void __launch_bounds__(D32_THREADS) design32(D32Params P) {
   L.zy = dp; dp += ld;
   L.kx = dp; dp += ld;
   L.dred = dp; dp += 4 * D32_WARPS;
-  L.dscal = dp; dp += 4;
   float* fp = reinterpret_cast<float*>(dp);
   L.Lf = fp; fp += ld * L.ldf;
   L.zf = fp; fp += ld;
   L.Sf = fp; fp += ld * PP;
   L.xf = fp; fp += PP;
-  L.lof = fp; fp += PP;
-  L.hif = fp; fp += PP;
-  L.kzf = fp; fp += (SEARCH == 0) ? exh_pass(ld) * L.ldf : D32_WARPS * ld;
-  L.rz = fp; fp += D32_WARPS * PP;
-  L.rA = fp; fp += R * PP;
-  L.rE = fp; fp += R * PP;
-  L.ralc = fp; fp += R;
-  L.rs = fp; fp += R;
-  L.xs = fp; fp += PP;
+  L.vs = fp; fp += P.nc_max;
+  L.ns = fp; fp += P.nc_max;
+  L.kxc = fp; fp += P.nc_max;
   L.red = fp; fp += 4 * D32_WARPS;
   int* ip = reinterpret_cast<int*>(fp);
   L.sel = ip; ip += ld;
-  L.starts = ip; ip += R;
-  L.rnev = ip; ip += R;
   L.ired = ip; ip += 2 * D32_WARPS + 2;
   L.used = reinterpret_cast<unsigned char*>(ip);
   L.neg_inv_theta = (float)(-1.0 / P.theta);
@@ -317,40 +331,41 @@ __global__ void __launch_bounds__(D32_THREADS) design32(D32Params P) {
     const int32_t* cl = P.cand + loc * P.nc_max;
     L.j = 0;
 
-    for (int r = tid; r < nc; r += blockDim.x) L.used[r] = 0;
     if (tid < p) L.xq[tid] = P.xref[loc * p + tid];
-    if (tid < PP) {
-      const bool in = tid < p;
-      L.xf[tid] = in ? (float)(P.xref[loc * p + tid] - P.center[tid]) : 0.f;
-      L.lof[tid] = in ? (float)(P.lo[tid] - P.center[tid]) : 0.f;
-      L.hif[tid] = in ? (float)(P.hi[tid] - P.center[tid]) : 0.f;
-    }
+    if (tid < PP) L.xf[tid] = tid < p ? (float)(P.xref[loc * p + tid] - P.center[tid]) : 0.f;
     for (int i = tid; i < ld * L.ldf; i += blockDim.x) L.Lf[i] = 0.f;
     if (P.tie_gap) for (int i = tid; i < ld; i += blockDim.x) P.tie_gap[loc * ld + i] = 0.0;
     if (P.nevals) for (int i = tid; i < ld; i += blockDim.x) P.nevals[loc * ld + i] = 0;
     __syncthreads();
+    for (int r = tid; r < nc; r += blockDim.x) {
+      L.used[r] = 0;
+      L.vs[r] = 0.f;
+      L.ns[r] = 0.f;
+      L.kxc[r] = __expf(sqdist_row32(cand_f(P, cl, r), L.xf, PP) * L.neg_inv_theta);
+    }
+    __syncthreads();
 
     bool ok = (n >= P.n0) && (n <= nc) && (n <= ld);
-    for (int r = 0; r < P.n0 && ok; ++r) ok = add_point32<SEARCH>(P, L, cl, nc, r, Lg, Kc_loc);
+    for (int r = 0; r < P.n0 && ok; ++r) ok = add_point32(P, L, cl, nc, r, Lg, Kc_loc);
     for (int j = P.n0; j < n && ok; ++j) {
       double gap = 0.0;
       int ne = 0;
-      int r = search_exh32(P, L, cl, nc, Kc_loc, &gap);
+      int r = search_exh32(L, nc, &gap);
       if (tid == 0) {
         if (P.tie_gap) P.tie_gap[loc * ld + (j - P.n0)] = gap;
         if (P.nevals) P.nevals[loc * ld + (j - P.n0)] = ne;
       }
-      ok = (r >= 0) && add_point32<SEARCH>(P, L, cl, nc, r, Lg, Kc_loc);
+      ok = (r >= 0) && add_point32(P, L, cl, nc, r, Lg, Kc_loc);
     }
     if (ok) {
-      double a = 0.0, b = 0.0, c = 0.0, dmy = 0.0;
+      double a = 0.0, b = 0.0, c = 0.0;
       for (int i = tid; i < L.j; i += blockDim.x) {
         a = fma(L.z[i], L.zy[i], a);
         b = fma(L.zy[i], L.zy[i], b);
         c = fma(L.z[i], L.z[i], c);
       }
-      block_sum2(a, b, L.dred);
-      block_sum2(c, dmy, L.dred);
+      sum_to_thread0(a, b, L.j, L.dred);
+      sum_to_thread0(c, L.j, L.dred + 2 * D32_WARPS);
       if (tid == 0) {
         P.mean[loc] = a;
         P.s2[loc] = b * ((1.0 + P.g) - c) / (double)L.j;
@@ -366,13 +381,11 @@ __global__ void __launch_bounds__(D32_THREADS) design32(D32Params P) {
   }
 }
 
-static size_t smem_design32(int n_max, int p, int PP, int nc_max, int R, int search) {
+static size_t smem_design32(int n_max, int p, int PP, int nc_max) {
   const int ldf = n_max | 1;
-  size_t d = (size_t)n_max * p + p + 5 * n_max + 4 * D32_WARPS + 4;
-  size_t f = (size_t)n_max * ldf + n_max + (size_t)n_max * PP + 3 * PP +
-             (search == 0 ? (size_t)exh_pass(n_max) * ldf : (size_t)D32_WARPS * n_max) + D32_WARPS * PP +
-             2 * R * PP + 2 * R + PP + 4 * D32_WARPS;
-  size_t i = (size_t)n_max + 2 * R + 2 * D32_WARPS + 2;
+  size_t d = (size_t)n_max * p + p + 5 * n_max + 4 * D32_WARPS;
+  size_t f = (size_t)n_max * ldf + n_max + (size_t)n_max * PP + PP + 3 * (size_t)nc_max + 4 * D32_WARPS;
+  size_t i = (size_t)n_max + 2 * D32_WARPS + 2;
   return d * 8 + f * 4 + i * 4 + nc_max + 16;
 }
 
@@ -380,21 +393,21 @@ cudaError_t launch_exh32(const DesignArgs& a, cudaStream_t s) {
   D32Params P;
   P.X = a.X; P.Y = a.Y; P.p = a.p; P.PP = a.PP; P.Xf = a.ws->Xf; P.xref = a.xref; P.M = a.M;
   P.cand = a.cand; P.nc_max = a.nc_max; P.nc_loc = a.nc_loc; P.n0 = a.n0; P.n_max = a.n_max;
-  P.n_loc = a.n_loc; P.theta = a.theta; P.g = a.g; P.R = a.nrays; P.lo = a.ws->lo;
-  P.hi = a.ws->hi; P.center = a.ws->center; P.mean = a.mean; P.s2 = a.s2;
+  P.n_loc = a.n_loc; P.theta = a.theta; P.g = a.g;
+  P.center = a.ws->center; P.mean = a.mean; P.s2 = a.s2;
   P.selected = a.selected; P.tie_gap = a.tie_gap; P.nevals = a.nevals; P.Linv = a.ws->state64;
   P.Kc = a.ws->state32; P.status = a.ws->status;
   P.queue = a.ws->queue + 2; P.order = a.order; P.count = a.count;
-  size_t sm = smem_design32(a.n_max, a.p, a.PP, a.nc_max, a.nrays, 0);
+  size_t sm = smem_design32(a.n_max, a.p, a.PP, a.nc_max);
   cudaError_t err =
-      cudaFuncSetAttribute(design32<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      cudaFuncSetAttribute(design32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (err != cudaSuccess) return err;
-  const int64_t grid = persistent_grid(design32<0>, D32_THREADS, sm, a.M, exh_slots(a.ws->chunk), 1,
+  const int64_t grid = persistent_grid(design32, D32_THREADS, sm, a.M, exh_slots(a.ws->chunk), 1,
                                        a.tune.exh_occ);
   if (grid < 0) return cudaErrorInvalidValue;
   if ((err = cudaMemsetAsync(P.queue, 0, sizeof(unsigned), s)) != cudaSuccess) return err;
   prof_begin("design32_exhaustive", s);
-  design32<0><<<(unsigned)grid, D32_THREADS, sm, s>>>(P);
+  design32<<<(unsigned)grid, D32_THREADS, sm, s>>>(P);
   prof_end(s);
   return cudaGetLastError();
 }

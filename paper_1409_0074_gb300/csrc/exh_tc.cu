@@ -109,30 +109,45 @@ __device__ __forceinline__ void xld16(uint32_t addr, float (&v)[16]) {
 }
 
 // block sums of two values at once (one pass of shuffles and barriers)
-__device__ __forceinline__ void xsum2(double& a, double& b, double* red) {
+// Sums over the block of FP64 terms held only by threads below `active`, to
+// thread 0 (other threads keep partial values).  Only the warps holding terms
+// shuffle and thread 0 adds the warp totals in warp order: bit-identical to a
+// full block sum (the idle warps' totals are exact zeros) at a fraction of its
+// FP64 instructions, which are scarce on this part.  Every thread must call.
+__device__ __forceinline__ void xsum2_t0(double& a, double& b, int active, double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
+  const int aw = min((active + 31) >> 5, XT_THREADS / 32);
+  __syncthreads();   // earlier readers of red are done
+  if (warp < aw) {
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) { red[2 * warp] = a; red[2 * warp + 1] = b; }
   }
   __syncthreads();
-  if (lane == 0) { red[2 * warp] = a; red[2 * warp + 1] = b; }
-  __syncthreads();
-  double ta = 0.0, tb = 0.0;
-  for (int w = 0; w < XT_THREADS / 32; ++w) { ta += red[2 * w]; tb += red[2 * w + 1]; }
-  a = ta;
-  b = tb;
+  if (threadIdx.x == 0) {
+    double ta = 0.0, tb = 0.0;
+    for (int w = 0; w < aw; ++w) { ta += red[2 * w]; tb += red[2 * w + 1]; }
+    a = ta;
+    b = tb;
+  }
 }
 
-__device__ __forceinline__ double xsum(double v, double* red) {
+__device__ __forceinline__ void xsum_t0(double& v, int active, double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int aw = min((active + 31) >> 5, XT_THREADS / 32);
   __syncthreads();
-  if (lane == 0) red[warp] = v;
+  if (warp < aw) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp] = v;
+  }
   __syncthreads();
-  double t = 0.0;
-  for (int w = 0; w < XT_THREADS / 32; ++w) t += red[w];
-  return t;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < aw; ++w) t += red[w];
+    v = t;
+  }
 }
 
 struct XtSmem {
@@ -269,10 +284,16 @@ __global__ void __launch_bounds__(XT_THREADS, 2) exh_tc_kernel(XtParams P) {
         lv[i] = acc;
         vv = fma(acc, acc, vv);
       }
-      vv = xsum(vv, red);
-      const double v = (1.0 + P.g) - vv;
-      if (!(v > 0.0)) return false;
-      const double inv_d = 1.0 / sqrt(v);
+      // thread 0 forms the pivot v = 1 + g - |l|^2 and 1 / sqrt(v)
+      xsum_t0(vv, j, red);
+      if (tid == 0) {
+        const double v = (1.0 + P.g) - vv;
+        red[0] = v;
+        red[1] = v > 0.0 ? 1.0 / sqrt(v) : 0.0;
+      }
+      __syncthreads();
+      if (!(red[0] > 0.0)) return false;
+      const double inv_d = red[1];
       for (int k = tid; k <= j; k += XT_THREADS) {
         double rk = inv_d;
         if (k < j) rk = -coldot64_ilp8(lv, Lg, ld, k, j) * inv_d;
@@ -289,7 +310,7 @@ __global__ void __launch_bounds__(XT_THREADS, 2) exh_tc_kernel(XtParams P) {
         zz = fma(rk, kx[k], zz);
         zyy = fma(rk, ys[k], zyy);
       }
-      xsum2(zz, zyy, red);
+      xsum2_t0(zz, zyy, j + 1, red);
       if (tid == 0) {
         z[j] = zz;
         zy[j] = zyy;
@@ -444,9 +465,8 @@ __global__ void __launch_bounds__(XT_THREADS, 2) exh_tc_kernel(XtParams P) {
         b = fma(zy[i], zy[i], b);
         c = fma(z[i], z[i], c);
       }
-      a = xsum(a, red);
-      b = xsum(b, red);
-      c = xsum(c, red);
+      xsum2_t0(a, b, j, red);
+      xsum_t0(c, j, red + 4);
       if (tid == 0) {
         P.mean[loc] = a;
         P.s2[loc] = b * ((1.0 + P.g) - c) / (double)j;

@@ -105,7 +105,8 @@ bool make_shape(int64_t N, int p, int64_t M, int n0, int n, int N_close, int nra
   if (n0 < 1 || n0 > n || n > LAGP_MAX_N || n > N_close || N_close > N || N_close > 4096)
     return false;
   if (search != LAGP_EXHAUSTIVE && search != LAGP_RAY) return false;
-  if (precision != LAGP_FP64 && precision != LAGP_FP32_SCORE) return false;
+  if (precision != LAGP_FP64 && precision != LAGP_FP32_SCORE && precision != LAGP_FP32_SCORE_TC)
+    return false;
   if (N > (int64_t)0x7fffff00) return false;   // int32 design indices
   int R = nrays <= 0 ? p : nrays;
   if (!knn_only && search == LAGP_RAY && (R > LAGP_MAX_RAYS || R > N_close - n)) return false;
@@ -154,8 +155,17 @@ static cudaError_t run_design(const DesignArgs& a0, int search, int precision, b
     }
     return launch_ray32(a, s);
   }
-  // exhaustive: tensor-core scorer for local designs up to its size limit,
-  // CUDA-core scorer above it (decided per location)
+  // exhaustive, FP32_SCORE: the incremental CUDA-core scorer for every size
+  if (precision == LAGP_FP32_SCORE) {
+    if (uneven && a.tune.lpt) {
+      if ((e = launch_order(a, search, 0, 1, s)) != cudaSuccess) return e;
+      a.order = ws.order;
+      a.count = ws.order_count;
+    }
+    return launch_exh32(a, s);
+  }
+  // exhaustive, FP32_SCORE_TC: tensor-core scorer for local designs up to its
+  // size limit, CUDA-core scorer above it (decided per location)
   const int lim = exh_tc_max_n();
   if (!uneven) return a.n_max <= lim ? launch_exh_tc(a, s) : launch_exh32(a, s);
   const int split = a.n_max > lim ? lim : 0;

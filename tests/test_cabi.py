@@ -50,10 +50,15 @@ def test_workspace_sizes_and_argument_checks(lib):
         (100000, 4, 10, 50, 1000, 17, 1, 0),     # too many rays
         (100000, 4, 10, 50, 52, 4, 1, 0),        # nrays > N_close - n
         (100000, 4, 10, 50, 1000, 4, 2, 0),      # bad search
-        (100000, 4, 10, 50, 1000, 4, 1, 2),      # bad precision
+        (100000, 4, 10, 50, 1000, 4, 1, 3),      # bad precision
+        (100000, 4, 10, 50, 1000, 4, 1, -1),     # bad precision
     ]
     for args in bad:
         assert lagp.laGP_workspace_bytes(*args) == 0, args
+    # both FP32-scoring forms are valid and share one workspace layout
+    f32 = [lagp.laGP_workspace_bytes(100000, 8, 10000, 50, 1000, 8, lagp.LAGP_EXHAUSTIVE, pr)
+           for pr in (lagp.LAGP_FP32_SCORE, lagp.LAGP_FP32_SCORE_TC)]
+    assert f32[0] > 0 and f32[0] == f32[1]
     assert lagp.laGP_knn_workspace_bytes(1000, 3, 10, 1) > 0
     assert lagp.laGP_host_workspace_bytes(1000, 3, 10, 10, 100, 2, 1, 1) > \
         lagp.laGP_workspace_bytes(1000, 3, 10, 10, 100, 2, 1, 1)

@@ -31,11 +31,11 @@ def uneven():
     return W.uneven_8d(M=4000)
 
 
-def _run(L, w, search, M=None, **kw):
+def _run(L, w, search, M=None, precision="fp32", **kw):
     import torch
     M = M or w.M
     out = L.predict(to_dev(w.X), to_dev(w.Y), to_dev(w.Xref[:M]), w.n0, int(w.n_arr.max()),
-                    int(w.nc_arr.max()), w.theta, w.g, search=search, nrays=8, precision="fp32",
+                    int(w.nc_arr.max()), w.theta, w.g, search=search, nrays=8, precision=precision,
                     n_loc=to_dev(w.n_arr[:M], torch.int32),
                     nclose_loc=to_dev(w.nc_arr[:M], torch.int32), want_trace=True, **kw)
     torch.cuda.synchronize()
@@ -47,8 +47,11 @@ def _same(a, b):
         np.testing.assert_array_equal(a[k], b[k], err_msg=k)
 
 
-@pytest.mark.parametrize("search", ["ray", "exhaustive"])
-def test_launch_choices_do_not_change_results(lagp, uneven, search):
+FORMS = [("ray", "fp32"), ("exhaustive", "fp32"), ("exhaustive", "fp32_tc")]
+
+
+@pytest.mark.parametrize("search,precision", FORMS)
+def test_launch_choices_do_not_change_results(lagp, uneven, search, precision):
     n, nc = int(uneven.n_arr.max()), int(uneven.nc_arr.max())
     s = lagp.SEARCH[search]
     M = 1500 if search == "ray" else 600
@@ -59,7 +62,7 @@ def test_launch_choices_do_not_change_results(lagp, uneven, search):
         for code in codes:
             lagp.laGP_tune_set(8, n, nc, 8, s, 1, code)
             assert lagp.laGP_tune_get(8, n, nc, 8, s, 1) == code
-            got = _run(lagp, uneven, search, M)
+            got = _run(lagp, uneven, search, M, precision)
             if ref is None:
                 ref = got
             else:
@@ -87,12 +90,12 @@ def test_autotune_stores_a_choice_and_keeps_results(lagp, uneven):
     _same(ref, _run(lagp, w, "ray", M))
 
 
-@pytest.mark.parametrize("search", ["ray", "exhaustive"])
-def test_uneven_fp32_form_vs_oracle(lagp, uneven, search):
+@pytest.mark.parametrize("search,precision", FORMS)
+def test_uneven_fp32_form_vs_oracle(lagp, uneven, search, precision):
     """Per-location n ~ U{20..100}, N' ~ U{300..2000}: sampled locations against
     the oracle run with the same per-location sizes."""
     M = 160 if search == "ray" else 96
-    g = _run(lagp, uneven, search, M)
+    g = _run(lagp, uneven, search, M, precision)
     o = oracle.predict(uneven.X, uneven.Y, uneven.Xref[:M], uneven.n0, int(uneven.n_arr.max()),
                        int(uneven.nc_arr.max()), uneven.theta, uneven.g, search, nrays=8,
                        n_arr=uneven.n_arr[:M], nc_arr=uneven.nc_arr[:M], nthreads=0)
@@ -103,6 +106,26 @@ def test_uneven_fp32_form_vs_oracle(lagp, uneven, search):
     # each location's design has exactly its own n points
     assert np.array_equal((g["selected"] >= 0).sum(axis=1), uneven.n_arr[:M])
     check_fp32_form(s, g, o, rmse_tol=0.05, max_gap=1e-3 if search == "ray" else None)
+
+
+def test_uneven_exhaustive_equals_uniform_calls(lagp, uneven):
+    """FP32-scoring exhaustive search: a location's result in a call with
+    uneven sizes is bit-identical to a uniform call with that location's own n
+    and N' (its arithmetic does not depend on the batch's maxima or on which
+    other locations share the launch)."""
+    import torch
+    w = uneven
+    M = 24
+    g = _run(lagp, w, "exhaustive", M)
+    X, Y = to_dev(w.X), to_dev(w.Y)
+    for i in range(0, M, 3):
+        n, nc = int(w.n_arr[i]), int(w.nc_arr[i])
+        one = lagp.predict(X, Y, to_dev(w.Xref[i:i + 1]), w.n0, n, nc, w.theta, w.g,
+                           search="exhaustive", precision="fp32", want_trace=True)
+        torch.cuda.synchronize()
+        assert one["mean"].item() == g["mean"][i] and one["s2"].item() == g["s2"][i], i
+        np.testing.assert_array_equal(one["selected"].cpu().numpy()[0], g["selected"][i][:n])
+        assert (g["selected"][i][n:] == -1).all()
 
 
 @pytest.mark.parametrize("search,uneven_sizes", [("ray", False), ("exhaustive", True)])
@@ -145,20 +168,20 @@ def test_plan_replays_match_direct_calls(lagp, uneven, search, uneven_sizes):
     plan.close()
 
 
-@pytest.mark.parametrize("search", ["ray", "exhaustive"])
-def test_tiny_batches_match_a_large_batch(lagp, uneven, search):
+@pytest.mark.parametrize("search,precision", FORMS)
+def test_tiny_batches_match_a_large_batch(lagp, uneven, search, precision):
     """Calls with fewer locations than a CTA has warps: every warp still owns
     scratch; each location's result equals the same location's in a larger
     call."""
     n, nc = int(uneven.n_arr.max()), int(uneven.nc_arr.max())
     s = lagp.SEARCH[search]
-    big = _run(lagp, uneven, search, 64)
+    big = _run(lagp, uneven, search, 64, precision)
     before = lagp.laGP_tune_get(8, n, nc, 8, s, 1)
     try:
         for code in ((1 | 16, 2 | 16, 4 | 16) if search == "ray" else (2 | 16,)):
             lagp.laGP_tune_set(8, n, nc, 8, s, 1, code)
             for M in (1, 2, 3, 5):
-                small = _run(lagp, uneven, search, M)
+                small = _run(lagp, uneven, search, M, precision)
                 for k in ("mean", "s2", "selected"):
                     np.testing.assert_array_equal(small[k], big[k][:M], err_msg=(code, M, k))
     finally:

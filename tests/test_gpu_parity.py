@@ -286,15 +286,16 @@ def test_fp32_score_ray_paper_scale_4d_sample(lagp, paper4d):
     check_fp32_form(w, g, o, rmse_tol=0.03, max_gap=1e-3)
 
 
-def test_fp32_score_exhaustive_paper_scale_4d_sample(lagp, paper4d):
+@pytest.mark.parametrize("precision", ["fp32", "fp32_tc"])
+def test_fp32_score_exhaustive_paper_scale_4d_sample(lagp, paper4d, precision):
     """On the 4-d workload (theta = 0.25, g = 1e-6, cond K up to ~1e7) FP32
     scores cannot rank candidates whose v is below ~1e-5: their cancellation
     error is as large as v.  Over all 10,000 locations the FP32 exhaustive
-    design measured 17% above the FP64 RMSE (the FP64 form is the one for this
-    conditioning); the bar records that limit (25%) and the design checks
-    still hold."""
+    designs measured up to 17% above the FP64 RMSE (the FP64 form is the one
+    for this conditioning); the bar records that limit (25%) and the design
+    checks still hold."""
     w = _sample(paper4d, 500)
-    g = gpu_run(lagp, w, "exhaustive", "fp32")
+    g = gpu_run(lagp, w, "exhaustive", precision)
     o = oracle_run(w, "exhaustive")
     check_fp32_form(w, g, o, rmse_tol=0.25, max_gap=None)
 
@@ -304,17 +305,20 @@ def large8d():
     return W.large_8d(M=100_000)
 
 
-@pytest.mark.parametrize("search,n,M_or", [("ray", 50, 1500), ("exhaustive", 50, 1500),
-                                          ("exhaustive", 80, 400)])
-def test_fp32_score_large_8d_sample(lagp, large8d, search, n, M_or):
+@pytest.mark.parametrize("search,n,M_or,precision", [("ray", 50, 1500, "fp32"),
+                                                    ("exhaustive", 50, 1500, "fp32"),
+                                                    ("exhaustive", 50, 1500, "fp32_tc"),
+                                                    ("exhaustive", 80, 400, "fp32")])
+def test_fp32_score_large_8d_sample(lagp, large8d, search, n, M_or, precision):
     """The FP32-scoring form on its own workload (N = 1e6, p = 8, theta = 1)
     in the bench's launch configuration (all 100,000 locations in one call),
     checked against the oracle on M_or sampled locations: RMSE within 1%.
-    n = 50 exhaustive runs the tensor-core scorer, n = 80 the CUDA-core one."""
+    Exhaustive "fp32" runs the incremental CUDA-core scorer, "fp32_tc" the
+    tensor-core contraction (n <= 64)."""
     import torch
     w = large8d
     out = lagp.predict(to_dev(w.X), to_dev(w.Y), to_dev(w.Xref), w.n0, n, w.nc, w.theta, w.g,
-                       search=search, nrays=8, precision="fp32", want_trace=True)
+                       search=search, nrays=8, precision=precision, want_trace=True)
     torch.cuda.synchronize()
     idx = np.linspace(0, w.M - 1, M_or).astype(int)
     g = {k: v.cpu().numpy()[idx] for k, v in out.items()}
