@@ -66,7 +66,7 @@ struct D32Params {
 };
 
 struct L32 {
-  float* Lf;       // [n_max][ldf] FP32 copy of L^{-1}
+  float* Lf;       // [n_max] FP32 copy of the newest row of L^{-1}
   float* zf;       // [n_max]
   float* Sf;       // [n_max][PP] centred FP32 selected coordinates
   float* xf;       // [PP]
@@ -85,7 +85,7 @@ struct L32 {
   int* sel;        // [n_max]
   int* ired;       // [WARPS*2]
   unsigned char* used;
-  int j, ldf;
+  int j;
   float neg_inv_theta, onepg;
 };
 
@@ -212,11 +212,11 @@ __device__ bool add_point32(const D32Params& P, L32& L, const int32_t* cl, int n
     if (i < j) a0 = fma(L.l[i], Lg[(int64_t)i * ld + k], a0);
     const double rk = -(a0 + a1) * inv_d;
     Lg[(int64_t)j * ld + k] = rk;
-    L.Lf[j * L.ldf + k] = (float)rk;
+    L.Lf[k] = (float)rk;
   }
   if (tid == 0) {
     Lg[(int64_t)j * ld + j] = inv_d;
-    L.Lf[j * L.ldf + j] = (float)inv_d;
+    L.Lf[j] = (float)inv_d;
     L.sel[j] = r;
     L.used[r] = 1;
   }
@@ -243,7 +243,7 @@ __device__ bool add_point32(const D32Params& P, L32& L, const int32_t* cl, int n
   const int64_t ldc = P.nc_max;
   float* row = Kc_loc + (int64_t)j * ldc;
   const float* sj = L.Sf + j * P.PP;
-  const float* Lfj = L.Lf + j * L.ldf;
+  const float* Lfj = L.Lf;
   const float zj = L.zf[j];
   for (int q = tid; q < nc; q += blockDim.x) {
     row[q] = __expf(sqdist_row32(cand_f(P, cl, q), sj, P.PP) * L.neg_inv_theta);
@@ -293,7 +293,6 @@ __global__ void __launch_bounds__(D32_THREADS) design32(D32Params P) {
   float* Kc_loc = P.Kc + (int64_t)blockIdx.x * ld * P.nc_max;
 
   L32 L;
-  L.ldf = ld | 1;
   double* dp = reinterpret_cast<double*>(smem);
   L.S64 = dp; dp += ld * p;
   L.xq = dp; dp += p;
@@ -304,7 +303,7 @@ __global__ void __launch_bounds__(D32_THREADS) design32(D32Params P) {
   L.kx = dp; dp += ld;
   L.dred = dp; dp += 4 * D32_WARPS;
   float* fp = reinterpret_cast<float*>(dp);
-  L.Lf = fp; fp += ld * L.ldf;
+  L.Lf = fp; fp += ld;
   L.zf = fp; fp += ld;
   L.Sf = fp; fp += ld * PP;
   L.xf = fp; fp += PP;
@@ -333,7 +332,6 @@ __global__ void __launch_bounds__(D32_THREADS) design32(D32Params P) {
 
     if (tid < p) L.xq[tid] = P.xref[loc * p + tid];
     if (tid < PP) L.xf[tid] = tid < p ? (float)(P.xref[loc * p + tid] - P.center[tid]) : 0.f;
-    for (int i = tid; i < ld * L.ldf; i += blockDim.x) L.Lf[i] = 0.f;
     if (P.tie_gap) for (int i = tid; i < ld; i += blockDim.x) P.tie_gap[loc * ld + i] = 0.0;
     if (P.nevals) for (int i = tid; i < ld; i += blockDim.x) P.nevals[loc * ld + i] = 0;
     __syncthreads();
@@ -382,9 +380,8 @@ __global__ void __launch_bounds__(D32_THREADS) design32(D32Params P) {
 }
 
 static size_t smem_design32(int n_max, int p, int PP, int nc_max) {
-  const int ldf = n_max | 1;
   size_t d = (size_t)n_max * p + p + 5 * n_max + 4 * D32_WARPS;
-  size_t f = (size_t)n_max * ldf + n_max + (size_t)n_max * PP + PP + 3 * (size_t)nc_max + 4 * D32_WARPS;
+  size_t f = 2 * (size_t)n_max + (size_t)n_max * PP + PP + 3 * (size_t)nc_max + 4 * D32_WARPS;
   size_t i = (size_t)n_max + 2 * D32_WARPS + 2;
   return d * 8 + f * 4 + i * 4 + nc_max + 16;
 }

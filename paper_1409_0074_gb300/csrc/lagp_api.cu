@@ -54,10 +54,11 @@ size_t layout_request(const Shape& sh, void* base, Workspace* ws) {
   } else {
     const size_t slots = exh_slots(ch);
     s64 = sizeof(double) * slots * sh.n_max * sh.n_max;
-    // correlation cache: [n_max][nc_max] (CUDA-core scorer) or operand tiles
-    // (tensor-core scorer), the larger
+    // correlation cache per slot: [n_max][nc_max] (CUDA-core scorer), or for
+    // the tensor-core form also its operand tiles, the larger
     size_t per = (size_t)sh.n_max * sh.nc_max;
-    if (exh_tc_cache_floats(sh.nc_max) > per) per = exh_tc_cache_floats(sh.nc_max);
+    if (sh.precision == LAGP_FP32_SCORE_TC && exh_tc_cache_floats(sh.nc_max) > per)
+      per = exh_tc_cache_floats(sh.nc_max);
     s32 = sizeof(float) * slots * per;
   }
   w->state64 = static_cast<double*>(c.take(s64));

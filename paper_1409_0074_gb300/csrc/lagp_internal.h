@@ -41,7 +41,7 @@ struct Workspace {
 // exhaustive kernels: their FP64 / correlation scratch is per slot, so a
 // launch holds at most this many locations' state at a time.
 #define RAY_SLOTS 6144
-#define EXH_SLOTS 1024
+#define EXH_SLOTS 1216
 int ray32_slots(int64_t chunk);
 int exh_slots(int64_t chunk);
 // floats of the tensor-core scorer's correlation cache per CTA slot
