@@ -32,6 +32,15 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # SMs x FP32 lanes x FMA x 
 FP64_PEAK_TFLOPS = 1.25                               # GB300 FP64 rate
 
 
+def hbm_peak():
+    """Measured copy bandwidth (GB/s) and its source."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -152,24 +161,36 @@ class Clocks:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
-def ray32_traffic():
-    """DRAM bytes of one full-size ray32 launch from the committed ncu summary,
-    or None when the kernel's sources changed since that capture."""
+def profile_traffic(profile, sources, key):
+    """DRAM bytes from a committed ncu summary (the value of `key`), or None
+    when the kernel's sources changed since that capture."""
     import hashlib
     root = os.path.dirname(os.path.abspath(__file__))
-    path = os.path.join(root, "profiles", "ray32_sinusoid8d_N1e6_M1e5_dram.md")
+    path = os.path.join(root, "profiles", profile)
     try:
         fields = dict(l.split(": ", 1) for l in open(path).read().splitlines() if ": " in l and
-                      l.split(": ", 1)[0] in ("traffic_bytes_per_launch", "source_sha256_16"))
+                      l.split(": ", 1)[0] in (key, "source_sha256_16"))
         csrc = os.path.join(root, "paper_1409_0074_gb300", "csrc")
         h = hashlib.sha256()
-        for f in ("ray32.cu", "common.cuh"):
+        for f in sources:
             h.update(open(os.path.join(csrc, f), "rb").read())
         if h.hexdigest()[:16] != fields["source_sha256_16"].strip():
             return None
-        return float(fields["traffic_bytes_per_launch"])
+        return float(fields[key])
     except (OSError, KeyError, ValueError):
         return None
+
+
+def ray32_traffic():
+    """DRAM bytes of one full-size ray32 launch (100,000 locations)."""
+    return profile_traffic("ray32_sinusoid8d_N1e6_M1e5_dram.md", ("ray32.cu", "common.cuh"),
+                           "traffic_bytes_per_launch")
+
+
+def design32_traffic_per_location():
+    """DRAM bytes per location of the CUDA-core exhaustive scorer (n = 50, N' = 1000)."""
+    return profile_traffic("design32_sinusoid8d_M20000.md", ("design_fp32.cu", "common.cuh"),
+                           "traffic_bytes_per_location")
 
 
 def kernel_flops(name, w, nevals_sum_j):
@@ -183,6 +204,18 @@ def kernel_flops(name, w, nevals_sum_j):
         s1, s2 = nevals_sum_j      # sum over evaluations of j and of j^2
         return s2 + (5 + 3 * w["p"] + 2) * s1
     return None
+
+
+def kernel_bytes(name, w):
+    """Algorithmic DRAM bytes of one launch of the CUDA-core exhaustive scorer
+    (see the design notes): per location, step m = 1..n reads the cache rows
+    0..m-1 of the N' - m unselected candidates and writes one row of N', and
+    the candidates' FP32 rows are read once: 4 (sum_m m (N' - m) + n N' + PP N')."""
+    if name != "design32_exhaustive":
+        return None
+    n, nc, PP = w["n"], w["nc"], w["PP"]
+    per_loc = 4.0 * (sum(m * (nc - m) for m in range(1, n + 1)) + n * nc + PP * nc)
+    return per_loc * w["M_launch"]
 
 
 def run_ours(args, rank, world):
@@ -247,7 +280,19 @@ def run_ours(args, rank, world):
     work = kernel_flops(name, dict(N=N, p=p, M_launch=M / max(chunks, 1)),
                         (sum_j / max(chunks, 1), sum_j2 / max(chunks, 1)))
     roof = None
-    if work is not None:
+    nbytes = kernel_bytes(name, dict(n=w.n, nc=w.nc, PP=(p + 3) // 4 * 4,
+                                     M_launch=M / max(chunks, 1)))
+    if nbytes is not None:
+        per_launch_ms = tot_ms / launches
+        achieved = nbytes / (per_launch_ms / 1e3) / 1e9
+        peak, src = hbm_peak()
+        tpl = design32_traffic_per_location() if (w.n == 50 and w.nc == 1000 and w.p == 8
+                                                   and w.N == 1_000_000) else None
+        roof = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None if tpl is None else tpl * M / max(chunks, 1),
+                "peak_source": src, "launch_ms": per_launch_ms}
+    elif work is not None:
         per_launch_ms = tot_ms / launches
         achieved = work / (per_launch_ms / 1e3) / 1e12
         traffic = ray32_traffic() if (name == "ray32" and w.M == 100_000 and w.N == 1_000_000
@@ -445,7 +490,7 @@ def run_cpu_baseline(args, w, search, sample=None):
 
 
 def base_line(args, world, value, ms, w):
-    return {"metric": "locations/sec at N=1e6,d=8,n=50 (ray search)", "value": value,
+    return {"metric": "locations/sec at N=1e6,d=8,n=50 (%s search)" % args.search, "value": value,
             "unit": "locations/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps if ms is not None else None,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
