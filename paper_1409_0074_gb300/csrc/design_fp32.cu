@@ -59,6 +59,7 @@ struct D32Params {
   int32_t* nevals;
   double* Linv;          // [slots][n_max][n_max] FP64 inverse factor
   float* Kc;             // exhaustive: [slots][n_max][nc_max] FP32 correlation cache
+  float* crow;           // [slots][nc_max][PP] the location's candidates' FP32 rows
   unsigned* status;
   unsigned* queue;       // work counter (zero at launch)
   const int32_t* order;  // item -> location, or null
@@ -165,18 +166,19 @@ __device__ VI block_best(VI t, float* fs, int* is) {
   return r;
 }
 
-__device__ __forceinline__ const float* cand_f(const D32Params& P, const int32_t* cl, int r) {
-  return P.Xf + (int64_t)cl[r] * P.PP;
+// candidate rank r's FP32 row, from the slot's gathered copy
+__device__ __forceinline__ const float* cand_f(const D32Params& P, const float* crow, int r) {
+  return crow + (int64_t)r * P.PP;
 }
 
 // Append candidate rank r: FP64 factor row, z, L^{-1}y, FP32 copies, the
 // correlation-cache row K(S_j, c) and entry j of every unselected candidate's w.
-__device__ bool add_point32(const D32Params& P, L32& L, const int32_t* cl, int nc, int r,
-                            double* Lg, float* Kc_loc) {
+__device__ bool add_point32(const D32Params& P, L32& L, const int32_t* cl, const float* crow,
+                            int nc, int r, double* Lg, float* Kc_loc) {
   const int tid = threadIdx.x, p = P.p, j = L.j, ld = P.n_max;
   const double* c = P.X + (int64_t)cl[r] * p;
   if (tid < p) L.S64[j * p + tid] = c[tid];
-  if (tid < P.PP) L.Sf[j * P.PP + tid] = cand_f(P, cl, r)[tid];
+  if (tid < P.PP) L.Sf[j * P.PP + tid] = cand_f(P, crow, r)[tid];
   __syncthreads();
   const double nit64 = -1.0 / P.theta;
   // correlations of the new point with the design, and with x (thread j)
@@ -239,24 +241,31 @@ __device__ bool add_point32(const D32Params& P, L32& L, const int32_t* cl, int n
   // the entry w_cj = row_j . K(S_{0..j}, c); |w_c|^2 and w_c . z are running
   // sums in the order i = 0, 1, ..., the same FP32 operations a from-scratch
   // evaluation at every step would perform.  Thread q owns candidates
-  // q, q + blockDim, ..., so the cache row it writes is the one it reads back.
+  // q, q + blockDim, ..., and takes the newest entry from the register that
+  // computed it.  Even terms go to a0 and odd terms to a1, in ascending order.
   const int64_t ldc = P.nc_max;
   float* row = Kc_loc + (int64_t)j * ldc;
   const float* sj = L.Sf + j * P.PP;
   const float* Lfj = L.Lf;
   const float zj = L.zf[j];
   for (int q = tid; q < nc; q += blockDim.x) {
-    row[q] = __expf(sqdist_row32(cand_f(P, cl, q), sj, P.PP) * L.neg_inv_theta);
+    const float kv = __expf(sqdist_row32(cand_f(P, crow, q), sj, P.PP) * L.neg_inv_theta);
+    row[q] = kv;
     if (L.used[q]) continue;
     const float* kc = Kc_loc + q;
     float a0 = 0.f, a1 = 0.f;
     int k = 0;
 #pragma unroll 4
-    for (; k + 1 <= j; k += 2) {
+    for (; k + 2 <= j; k += 2) {
       a0 = fmaf(Lfj[k], kc[k * ldc], a0);
       a1 = fmaf(Lfj[k + 1], kc[(k + 1) * ldc], a1);
     }
-    if (k <= j) a0 = fmaf(Lfj[k], kc[k * ldc], a0);
+    if (k == j) {
+      a0 = fmaf(Lfj[j], kv, a0);
+    } else {
+      a0 = fmaf(Lfj[k], kc[k * ldc], a0);
+      a1 = fmaf(Lfj[j], kv, a1);
+    }
     const float w = a0 + a1;
     L.vs[q] = fmaf(w, w, L.vs[q]);
     L.ns[q] = fmaf(w, zj, L.ns[q]);
@@ -284,13 +293,14 @@ __device__ int search_exh32(const L32& L, int nc, double* gap_out) {
   return b.i;
 }
 
-__global__ void __launch_bounds__(D32_THREADS) design32(D32Params P) {
+__global__ void __launch_bounds__(D32_THREADS, 6) design32(D32Params P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned s_item;
   const int tid = threadIdx.x, p = P.p, PP = P.PP, ld = P.n_max;
   // scratch of this CTA slot
   double* Lg = P.Linv + (int64_t)blockIdx.x * ld * ld;
   float* Kc_loc = P.Kc + (int64_t)blockIdx.x * ld * P.nc_max;
+  float* crow = P.crow + (int64_t)blockIdx.x * P.nc_max * PP;
 
   L32 L;
   double* dp = reinterpret_cast<double*>(smem);
@@ -334,17 +344,23 @@ __global__ void __launch_bounds__(D32_THREADS) design32(D32Params P) {
     if (tid < PP) L.xf[tid] = tid < p ? (float)(P.xref[loc * p + tid] - P.center[tid]) : 0.f;
     if (P.tie_gap) for (int i = tid; i < ld; i += blockDim.x) P.tie_gap[loc * ld + i] = 0.0;
     if (P.nevals) for (int i = tid; i < ld; i += blockDim.x) P.nevals[loc * ld + i] = 0;
+    // the candidates' FP32 rows, gathered once into the slot in rank order
+    for (int e = tid; e < nc * (PP >> 2); e += blockDim.x) {
+      const int q = e / (PP >> 2), c4 = (e - q * (PP >> 2)) << 2;
+      *reinterpret_cast<float4*>(crow + (int64_t)q * PP + c4) =
+          *reinterpret_cast<const float4*>(P.Xf + (int64_t)cl[q] * PP + c4);
+    }
     __syncthreads();
     for (int r = tid; r < nc; r += blockDim.x) {
       L.used[r] = 0;
       L.vs[r] = 0.f;
       L.ns[r] = 0.f;
-      L.kxc[r] = __expf(sqdist_row32(cand_f(P, cl, r), L.xf, PP) * L.neg_inv_theta);
+      L.kxc[r] = __expf(sqdist_row32(cand_f(P, crow, r), L.xf, PP) * L.neg_inv_theta);
     }
     __syncthreads();
 
     bool ok = (n >= P.n0) && (n <= nc) && (n <= ld);
-    for (int r = 0; r < P.n0 && ok; ++r) ok = add_point32(P, L, cl, nc, r, Lg, Kc_loc);
+    for (int r = 0; r < P.n0 && ok; ++r) ok = add_point32(P, L, cl, crow, nc, r, Lg, Kc_loc);
     for (int j = P.n0; j < n && ok; ++j) {
       double gap = 0.0;
       int ne = 0;
@@ -353,7 +369,7 @@ __global__ void __launch_bounds__(D32_THREADS) design32(D32Params P) {
         if (P.tie_gap) P.tie_gap[loc * ld + (j - P.n0)] = gap;
         if (P.nevals) P.nevals[loc * ld + (j - P.n0)] = ne;
       }
-      ok = (r >= 0) && add_point32(P, L, cl, nc, r, Lg, Kc_loc);
+      ok = (r >= 0) && add_point32(P, L, cl, crow, nc, r, Lg, Kc_loc);
     }
     if (ok) {
       double a = 0.0, b = 0.0, c = 0.0;
@@ -393,7 +409,7 @@ cudaError_t launch_exh32(const DesignArgs& a, cudaStream_t s) {
   P.n_loc = a.n_loc; P.theta = a.theta; P.g = a.g;
   P.center = a.ws->center; P.mean = a.mean; P.s2 = a.s2;
   P.selected = a.selected; P.tie_gap = a.tie_gap; P.nevals = a.nevals; P.Linv = a.ws->state64;
-  P.Kc = a.ws->state32; P.status = a.ws->status;
+  P.Kc = a.ws->state32; P.crow = a.ws->crow; P.status = a.ws->status;
   P.queue = a.ws->queue + 2; P.order = a.order; P.count = a.count;
   size_t sm = smem_design32(a.n_max, a.p, a.PP, a.nc_max);
   cudaError_t err =
