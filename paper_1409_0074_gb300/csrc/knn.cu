@@ -163,7 +163,12 @@ __global__ void __launch_bounds__(KNN_WARPS * 32)
 knn_pilot(const float* __restrict__ Xf, const float* __restrict__ nx, int64_t N, int64_t S, int p,
           const double* __restrict__ xref, int64_t M, const double* __restrict__ center,
           int nc_max, const int32_t* __restrict__ nc_loc, int cap, float* __restrict__ thr_out) {
+  // the sample rows pass through shared memory a tile at a time, shared by
+  // the CTA's warps (each sample row is read from L2 once per CTA and pass)
+  constexpr int T = 2048 / PP;
   __shared__ uint32_t hist[KNN_WARPS][KNN_QW][256];
+  __shared__ __align__(16) float sx[T * PP];
+  __shared__ float sn[T];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t q0 = (int64_t)blockIdx.x * (KNN_WARPS * KNN_QW) + warp * KNN_QW;
   float qf[KNN_QW][PP], nq[KNN_QW];
@@ -194,21 +199,31 @@ knn_pilot(const float* __restrict__ Xf, const float* __restrict__ nx, int64_t N,
   for (int pass = 0; pass < 2; ++pass) {
     for (int i = lane; i < KNN_QW * 256; i += 32) (&hist[warp][0][0])[i] = 0u;
     __syncwarp();
-    for (int64_t i = lane; i < S; i += 32) {
-      const int64_t row = i * stride;
-      float xv[PP];
-#pragma unroll
-      for (int k = 0; k < PP; k += 4) {
-        const float4 v4 = __ldg(reinterpret_cast<const float4*>(Xf + row * PP + k));
-        xv[k] = v4.x; xv[k + 1] = v4.y; xv[k + 2] = v4.z; xv[k + 3] = v4.w;
+    for (int64_t t0 = 0; t0 < S; t0 += T) {
+      const int cnt = (int)(S - t0 < T ? S - t0 : T);
+      __syncthreads();   // the previous tile is consumed
+      for (int e = threadIdx.x; e < cnt * (PP / 4); e += blockDim.x) {
+        const int r = e / (PP / 4), c4 = (e - r * (PP / 4)) * 4;
+        *reinterpret_cast<float4*>(sx + r * PP + c4) =
+            __ldg(reinterpret_cast<const float4*>(Xf + (t0 + r) * stride * PP + c4));
       }
-      float d[KNN_QW];
-      knn_d4<PP>(qf, nq, xv, __ldg(nx + row), d);
+      for (int e = threadIdx.x; e < cnt; e += blockDim.x) sn[e] = __ldg(nx + (t0 + e) * stride);
+      __syncthreads();
+      for (int i = lane; i < cnt; i += 32) {
+        float xv[PP];
 #pragma unroll
-      for (int a = 0; a < KNN_QW; ++a) {
-        const uint32_t bits = __float_as_uint(fmaxf(d[a], 0.f));
-        if (pass == 0) atomicAdd(&hist[warp][a][bits >> 23], 1u);
-        else if ((bits >> 23) == b1[a]) atomicAdd(&hist[warp][a][(bits >> 15) & 255u], 1u);
+        for (int k = 0; k < PP; k += 4) {
+          const float4 v4 = *reinterpret_cast<const float4*>(sx + i * PP + k);
+          xv[k] = v4.x; xv[k + 1] = v4.y; xv[k + 2] = v4.z; xv[k + 3] = v4.w;
+        }
+        float d[KNN_QW];
+        knn_d4<PP>(qf, nq, xv, sn[i], d);
+#pragma unroll
+        for (int a = 0; a < KNN_QW; ++a) {
+          const uint32_t bits = __float_as_uint(fmaxf(d[a], 0.f));
+          if (pass == 0) atomicAdd(&hist[warp][a][bits >> 23], 1u);
+          else if ((bits >> 23) == b1[a]) atomicAdd(&hist[warp][a][(bits >> 15) & 255u], 1u);
+        }
       }
     }
     __syncwarp();
