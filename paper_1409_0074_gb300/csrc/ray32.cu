@@ -222,21 +222,31 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
   // ---- append candidate rank rr to the design (FP64 factor row) ----
   auto add_point = [&](int rr) -> bool {
     const double* c64 = P.X + (int64_t)cl[rr] * p;
-    for (int i = lane; i < j; i += 32)
-      kv64[i] = corr64_fast(P.X + (int64_t)cl[sel[i]] * p, c64, p, nit64);
+    for (int i = lane; i <= j; i += 32) {
+      if (i < j) kv64[i] = corr64_fast(P.X + (int64_t)cl[sel[i]] * p, c64, p, nit64);
+      else kx64[j] = corr64_fast(c64, xq, p, nit64);
+    }
     __syncwarp();
-    double vv = 0.0;
+    // l = L_j^{-1} k_j(x_new); v = 1 + g - |l|^2, d = sqrt(v), and by forward
+    // substitution z_j = (K(x_new, x) - l . z) / d, (L^{-1} y)_j =
+    // (y_new - l . L^{-1} y) / d, all from one pass.  A warp's FP64
+    // instruction costs the same whatever its active lanes, so every lane
+    // evaluates the scalar tail.
+    double vv = 0.0, lz = 0.0, lzy = 0.0;
     for (int i = lane; i < j; i += 32) {
-      const double* Li = Lg + tri(i);
-      const double acc = dot64_ilp(Li, kv64, i + 1);
+      const double acc = dot64_ilp(Lg + tri(i), kv64, i + 1);
       l64[i] = acc;
       vv = fma(acc, acc, vv);
+      lz = fma(acc, z64[i], lz);
+      lzy = fma(acc, zy64[i], lzy);
     }
     vv = warp_sum64(vv);
+    lz = warp_sum64(lz);
+    lzy = warp_sum64(lzy);
     __syncwarp();
     const double v = (1.0 + P.g) - vv;
     if (!(v > 0.0)) return false;
-    const double inv_d = 1.0 / sqrt(v);
+    const double inv_d = rsqrt(v);
     double* Lj = Lg + tri(j);
     float* Lfj = Lf + roff(j);
     for (int k = lane; k < j; k += 32) {
@@ -247,33 +257,21 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
         a1 = fma(l64[i + 1], Lg[tri(i + 1) + k], a1);
       }
       if (i < j) a0 = fma(l64[i], Lg[tri(i) + k], a0);
-      const double acc = a0 + a1;
-      const double rk = -acc * inv_d;
+      const double rk = -(a0 + a1) * inv_d;
       Lj[k] = rk;
       Lfj[k] = (float)rk;
     }
     if (lane == 0) {
       Lj[j] = inv_d;
       Lfj[j] = (float)inv_d;
-      kx64[j] = corr64_fast(c64, xq, p, nit64);
       sel[j] = rr;
       mask[rr >> 5] |= 1u << (rr & 31);
+      const double zj = (kx64[j] - lz) * inv_d;
+      z64[j] = zj;
+      zy64[j] = (P.Y[cl[rr]] - lzy) * inv_d;
+      zf[j] = (float)zj;
     }
     if (lane < PP) Sf[j * PP + lane] = P.Xf[(int64_t)cl[rr] * PP + lane];
-    __syncwarp();
-    double zz = 0.0, zyy = 0.0;
-    for (int k = lane; k <= j; k += 32) {
-      const double rk = Lj[k];
-      zz = fma(rk, kx64[k], zz);
-      zyy = fma(rk, P.Y[cl[sel[k]]], zyy);
-    }
-    zz = warp_sum64(zz);
-    zyy = warp_sum64(zyy);
-    if (lane == 0) {
-      z64[j] = zz;
-      zy64[j] = zyy;
-      zf[j] = (float)zz;
-    }
     __syncwarp();
     ++j;
     return true;
