@@ -1,7 +1,8 @@
 // design_fp32.cu -- exhaustive greedy local design with FP32 candidate scoring
-// and an FP64 factor update, one CTA per predictive location, for designs
-// larger than the tensor-core scorer takes (the ray search of this form is in
-// ray32.cu).
+// and an FP64 factor update, one CTA per predictive location: the exhaustive
+// search of the LAGP_FP32_SCORE form for every n, and of LAGP_FP32_SCORE_TC
+// for the designs larger than its tensor-core scorer (exh_tc.cu) takes.  The
+// ray search of these forms is in ray32.cu.
 //
 // Scoring form.  With K_j = L_j L_j^T (Cholesky) the ALC integrand of Eq. alc
 // (sign reading as in the FP64 path) becomes

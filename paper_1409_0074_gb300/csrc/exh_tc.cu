@@ -1,7 +1,9 @@
 // exh_tc.cu -- exhaustive greedy local design (Gramacy & Haaland, Sec 2.2) with
 // the candidate scores of every step computed as a dense contraction on the
 // tensor cores, one CTA (4 warps) per predictive location; local designs up to
-// n = 64.
+// n = 64.  This is the exhaustive search of the LAGP_FP32_SCORE_TC form; the
+// default LAGP_FP32_SCORE form keeps running sums instead and only adds the
+// newest column of W per step (design_fp32.cu).
 //
 // Scoring (the factored form of Eq. alc, as in design_fp32.cu): with the
 // correlation rows Kc (N' x j, Kc[r][i] = K(c_r, S_i)) and the inverse

@@ -191,12 +191,14 @@ cudaError_t launch_design_fp64(const DesignArgs& a, int search, cudaStream_t s);
 // FP32-scoring ray search, one warp per location (ray32.cu); its per-location
 // FP64 scratch in Workspace::state64 holds ray32_g64_doubles(n_max) doubles.
 cudaError_t launch_ray32(const DesignArgs& a, cudaStream_t s);
-// FP32-scoring exhaustive search with tensor-core scoring (exh_tc.cu) for the
-// locations with n <= exh_tc_max_n().
+// Exhaustive search of the LAGP_FP32_SCORE_TC form, tensor-core scoring
+// (exh_tc.cu), for the locations with n <= exh_tc_max_n().
 int exh_tc_max_n();
 cudaError_t launch_exh_tc(const DesignArgs& a, cudaStream_t s);
 size_t ray32_g64_doubles(int n_max);
-// FP32-scoring exhaustive search with CUDA-core scoring (design_fp32.cu), n_max <= 128.
+// FP32-scoring exhaustive search with incremental CUDA-core scoring
+// (design_fp32.cu), n_max <= 128: every location of the LAGP_FP32_SCORE form,
+// the n > exh_tc_max_n() locations of LAGP_FP32_SCORE_TC.
 cudaError_t launch_exh32(const DesignArgs& a, cudaStream_t s);
 
 }  // namespace lagp
