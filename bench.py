@@ -164,21 +164,32 @@ class Clocks:
 def profile_traffic(profile, sources, key):
     """DRAM bytes from a committed ncu summary (the value of `key`), or None
     when the kernel's sources changed since that capture."""
-    import hashlib
     root = os.path.dirname(os.path.abspath(__file__))
     path = os.path.join(root, "profiles", profile)
     try:
         fields = dict(l.split(": ", 1) for l in open(path).read().splitlines() if ": " in l and
                       l.split(": ", 1)[0] in (key, "source_sha256_16"))
         csrc = os.path.join(root, "paper_1409_0074_gb300", "csrc")
-        h = hashlib.sha256()
-        for f in sources:
-            h.update(open(os.path.join(csrc, f), "rb").read())
-        if h.hexdigest()[:16] != fields["source_sha256_16"].strip():
+        if source_hash([open(os.path.join(csrc, f)).read() for f in sources]) != \
+                fields["source_sha256_16"].strip():
             return None
         return float(fields[key])
     except (OSError, KeyError, ValueError):
         return None
+
+
+def source_hash(texts):
+    """First 16 hex digits of the sha256 of the sources' code: `//` comments,
+    trailing blanks and empty lines removed, so that a comment edit keeps a
+    capture valid and any code change voids it."""
+    import hashlib
+    h = hashlib.sha256()
+    for t in texts:
+        for line in t.splitlines():
+            code = line.split("//", 1)[0].rstrip()
+            if code:
+                h.update(code.encode() + b"\n")
+    return h.hexdigest()[:16]
 
 
 def ray32_traffic():

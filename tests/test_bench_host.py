@@ -1,0 +1,54 @@
+"""Host-side pieces of bench.py that decide what the bench line reports: the
+algorithmic bytes of the exhaustive scorer and the source hash that keeps a
+committed DRAM capture valid (CPU only)."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_exhaustive_bytes_by_brute_force():
+    """Per location: step m = 1..n reads rows 0..m-1 of the N' - m unselected
+    candidates' cache columns and writes one row of N'; the candidate rows
+    (PP floats each) are read once.  Counted here element by element."""
+    n, nc, PP = 7, 40, 4
+    reads = 0
+    for m in range(1, n + 1):
+        for _cand in range(nc - m):
+            reads += m
+    want = 4 * (reads + n * nc + PP * nc)
+    got = bench.kernel_bytes("design32_exhaustive", dict(n=n, nc=nc, PP=PP, M_launch=3))
+    assert got == 3 * want
+    assert bench.kernel_bytes("ray32", dict(n=n, nc=nc, PP=PP, M_launch=3)) is None
+
+
+def test_exhaustive_bytes_at_the_bench_workload():
+    per_loc = bench.kernel_bytes("design32_exhaustive", dict(n=50, nc=1000, PP=8, M_launch=1))
+    assert per_loc == pytest.approx(5.16e6, rel=1e-3)
+
+
+def test_source_hash_ignores_comments_only():
+    a = "int f(int x) {  // add one\n  return x + 1;\n}\n"
+    b = "// header comment\n\nint f(int x) {  // plus one\n  return x + 1;   \n}\n"
+    c = "int f(int x) {\n  return x + 2;\n}\n"
+    assert bench.source_hash([a]) == bench.source_hash([b])
+    assert bench.source_hash([a]) != bench.source_hash([c])
+    assert bench.source_hash([a, c]) != bench.source_hash([c, a])
+
+
+def test_committed_captures_are_read():
+    """Each committed capture yields its own figure while the code matches,
+    and nothing otherwise (never another figure)."""
+    for path, key, fn in [("design32_sinusoid8d_M20000.md", "traffic_bytes_per_location",
+                           bench.design32_traffic_per_location),
+                          ("ray32_sinusoid8d_N1e6_M1e5_dram.md", "traffic_bytes_per_launch",
+                           bench.ray32_traffic)]:
+        text = open(os.path.join(ROOT, "profiles", path)).read()
+        stored = float(next(l.split(": ", 1)[1] for l in text.splitlines()
+                            if l.startswith(key + ": ")))
+        assert stored > 0
+        assert fn() in (None, stored)
