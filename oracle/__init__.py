@@ -8,6 +8,9 @@ benchmark's CPU-baseline leg are its only users.  The CUDA product path never
 imports it.  The arithmetic lives in lagp_oracle.c; this module marshals numpy
 arrays through ctypes.
 
+Local inference for the lengthscale (Sec 5, Eq. gpk): loglik, mle_theta and
+predict_mle, pinned in tests/test_oracle_mle.py.
+
 Every function here is pinned by tests under tests/ against closed forms,
 brute force or library routines (numpy, scipy).  Ray-search designs are pinned
 only piecewise (round-robin offsets, segments, Brent minima, snapping): the
@@ -53,6 +56,18 @@ def lib():
             dp, dp, C.c_int64, C.c_int, dp, C.c_int64, C.c_int, C.c_int, C.c_int,
             ip, ip, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
             dp, dp, ip, dp, ip, ip, C.c_int]
+        _lib.lagp_oracle_loglik.restype = C.c_double
+        _lib.lagp_oracle_loglik.argtypes = [dp, dp, C.c_int, C.c_int, C.c_double, C.c_double,
+                                            dp, dp]
+        _lib.lagp_oracle_mle_theta.restype = C.c_double
+        _lib.lagp_oracle_mle_theta.argtypes = [dp, dp, C.c_int, C.c_int, C.c_double,
+                                               C.c_double, C.c_double, C.c_double,
+                                               C.c_double, C.c_int, C.POINTER(C.c_int)]
+        _lib.lagp_oracle_predict_mle.restype = C.c_int
+        _lib.lagp_oracle_predict_mle.argtypes = [
+            dp, dp, C.c_int64, C.c_int, dp, C.c_int64, C.c_int, C.c_int, C.c_int,
+            C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int,
+            dp, dp, dp, ip, ip, C.c_int]
     return _lib
 
 
@@ -189,3 +204,51 @@ def predict(X, Y, Xref, n0, n, nc, theta, g, search="exhaustive", nrays=0,
                                      pm, ps, psel, pg, pne, pst, int(nthreads))
     return dict(mean=mean, s2=s2, selected=sel, gap=gap, nevals=nev, status=st,
                 threads=used)
+
+
+def loglik(S, y, theta, g):
+    """log p(y | K_theta) of Eq. gpk on the local design S (n x p) with
+    responses y, and its first and second derivatives in theta:
+    (value, d/dtheta, d2/dtheta2)."""
+    S, pS = _d(np.atleast_2d(S))
+    y, py = _d(y)
+    n, p = S.shape
+    d1, p1 = _d(np.zeros(1))
+    d2, p2 = _d(np.zeros(1))
+    v = lib().lagp_oracle_loglik(pS, py, n, p, float(theta), float(g), p1, p2)
+    return v, float(d1[0]), float(d2[0])
+
+
+def mle_theta(S, y, theta0, g, tmin, tmax, tol=1e-10, maxit=200):
+    """Safeguarded Newton maximiser of loglik over [tmin, tmax] from theta0
+    (Sec 5's local inference for the lengthscale).  Returns (theta, iters)."""
+    S, pS = _d(np.atleast_2d(S))
+    y, py = _d(y)
+    n, p = S.shape
+    it = C.c_int(0)
+    t = lib().lagp_oracle_mle_theta(pS, py, n, p, float(theta0), float(g), float(tmin),
+                                    float(tmax), float(tol), int(maxit), C.byref(it))
+    return t, it.value
+
+
+def predict_mle(X, Y, Xref, n0, n, nc, theta0, g, tmin, tmax, search="exhaustive", nrays=0,
+                stages=1, nthreads=1):
+    """Local designs coupled with local inference for theta: `stages` rounds of
+    (greedy design at the current theta, then the MLE on that design, starting
+    from theta0), and the predictive equations at the last estimate on the last
+    design.  Returns a dict with mean, s2, theta, selected, status, threads."""
+    X, pX = _d(X)
+    Y, pY = _d(Y)
+    Xref, pR = _d(np.atleast_2d(Xref))
+    N, p = X.shape
+    M = Xref.shape[0]
+    mean, pm = _d(np.zeros(M))
+    s2, ps = _d(np.zeros(M))
+    th, pt = _d(np.zeros(M))
+    sel, psel = _i(np.zeros((M, n), np.int32))
+    st, pst = _i(np.zeros(M, np.int32))
+    used = lib().lagp_oracle_predict_mle(pX, pY, N, p, pR, M, n0, n, nc, float(theta0),
+                                         float(g), float(tmin), float(tmax), SEARCH[search],
+                                         int(nrays), int(stages), pm, ps, pt, psel, pst,
+                                         int(nthreads))
+    return dict(mean=mean, s2=s2, theta=th, selected=sel, status=st, threads=used)

@@ -641,3 +641,307 @@ int lagp_oracle_predict(const double* X, const double* Y, int64_t N, int p,
     free(hi);
     return used_threads;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Local inference for the lengthscale (Sec 2.1, Eq. gpk; Sec 5: local designs */
+/* are coupled with Newton-like maximisation of the local posterior of theta, */
+/* optionally followed by a second-stage re-design at the estimate).          */
+/*                                                                            */
+/* Readings (listed in the design notes):                                     */
+/*   M1  the local posterior of theta is the marginal likelihood of Eq. gpk   */
+/*       (reference prior on tau^2) with a flat prior on theta over a         */
+/*       caller-given range [tmin, tmax]; the nugget g stays fixed.           */
+/*   M2  K_theta carries 1 + g on its diagonal (R2), so dK/dtheta has a zero  */
+/*       diagonal.                                                            */
+/*   M3  Newton's method on theta from a start theta0, safeguarded: a bracket */
+/*       [a, b] around the maximiser is kept from the sign of the first       */
+/*       derivative, and a step that leaves the bracket, or is taken where    */
+/*       the curvature is not negative, is replaced by the bracket's midpoint.*/
+/*       It stops when a step or the bracket is below tol * theta, or after   */
+/*       maxit iterations; a maximiser on a bound returns that bound.         */
+/*   M4  two stages: the design built at theta0 gives theta_1; the design     */
+/*       rebuilt at theta_1 gives theta_2; the prediction uses the last       */
+/*       estimate on the last design (one stage: theta_1 on the first design).*/
+/* ------------------------------------------------------------------------- */
+
+/* log Gamma(n/2) for an integer n >= 1 from Gamma(1) = 1, Gamma(1/2) = sqrt(pi)
+   and Gamma(z + 1) = z Gamma(z). */
+static double log_gamma_half(int n)
+{
+    double s = 0.0;
+    if (n % 2 == 0) {
+        for (int i = 1; i < n / 2; ++i) s = s + log((double)i);
+    } else {
+        s = 0.5 * log(M_PI);
+        for (int i = 0; i < (n - 1) / 2; ++i) s = s + log(0.5 + (double)i);
+    }
+    return s;
+}
+
+/* Plain Cholesky K = C C^T of an n x n symmetric matrix (row-major); C is
+   written to the lower triangle of Cm.  Returns -1 when K is not positive
+   definite. */
+static int cholesky(const double* K, int n, double* Cm)
+{
+    for (int j = 0; j < n; ++j) {
+        double s = K[j * n + j];
+        for (int k = 0; k < j; ++k) s = s - Cm[j * n + k] * Cm[j * n + k];
+        if (!(s > 0.0)) return -1;
+        const double cjj = sqrt(s);
+        Cm[j * n + j] = cjj;
+        for (int i = j + 1; i < n; ++i) {
+            double t = K[i * n + j];
+            for (int k = 0; k < j; ++k) t = t - Cm[i * n + k] * Cm[j * n + k];
+            Cm[i * n + j] = t / cjj;
+        }
+        for (int i = 0; i < j; ++i) Cm[i * n + j] = 0.0;
+    }
+    return 0;
+}
+
+/* K^{-1} = C^{-T} C^{-1} from the Cholesky factor; Ci receives C^{-1}. */
+static void chol_inverse(const double* Cm, int n, double* Ci, double* Kinv)
+{
+    for (int i = 0; i < n * n; ++i) Ci[i] = 0.0;
+    for (int c = 0; c < n; ++c) {              /* column c of C^{-1}: C w = e_c */
+        for (int i = c; i < n; ++i) {
+            double t = (i == c) ? 1.0 : 0.0;
+            for (int k = c; k < i; ++k) t = t - Cm[i * n + k] * Ci[k * n + c];
+            Ci[i * n + c] = t / Cm[i * n + i];
+        }
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double t = 0.0;
+            for (int k = 0; k < n; ++k) t = t + Ci[k * n + i] * Ci[k * n + j];
+            Kinv[i * n + j] = t;
+        }
+}
+
+/*
+ * log p(y | K_theta) of Eq. gpk for the design S (n x p) and responses y:
+ *   log Gamma(n/2) - (n/2) log(2 pi) - (1/2) log|K| - (n/2) log(psi / 2),
+ *   psi = y^T K^{-1} y,
+ * and, when d1 / d2 are not NULL, its first and second derivatives in theta:
+ *   K'_ab = K_ab d_ab / theta^2, K''_ab = K_ab (d_ab^2 / theta^4 - 2 d_ab / theta^3),
+ *   l'  = -(1/2) tr(K^{-1} K') - (n/2) psi' / psi,
+ *   l'' = -(1/2) [tr(K^{-1} K'') - tr(K^{-1} K' K^{-1} K')]
+ *         - (n/2) [psi'' / psi - (psi' / psi)^2],
+ *   psi' = -alpha^T K' alpha, psi'' = 2 (K' alpha)^T K^{-1} (K' alpha) - alpha^T K'' alpha,
+ *   alpha = K^{-1} y.
+ * Returns NAN when K is not positive definite.
+ */
+double lagp_oracle_loglik(const double* S, const double* y, int n, int p, double theta,
+                          double g, double* d1, double* d2)
+{
+    const size_t nn = (size_t)n * n;
+    double* D = (double*)malloc(sizeof(double) * nn);      /* squared distances */
+    double* K = (double*)malloc(sizeof(double) * nn);
+    double* Cm = (double*)malloc(sizeof(double) * nn);
+    double* Ci = (double*)malloc(sizeof(double) * nn);
+    double* Ki = (double*)malloc(sizeof(double) * nn);
+    double* K1 = (double*)malloc(sizeof(double) * nn);
+    double* K2 = (double*)malloc(sizeof(double) * nn);
+    double* A = (double*)malloc(sizeof(double) * nn);      /* K^{-1} K' */
+    double* al = (double*)malloc(sizeof(double) * (size_t)n);
+    double* u = (double*)malloc(sizeof(double) * (size_t)n);
+    double ll = NAN;
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b) {
+            const double d = lagp_oracle_sqdist(S + (size_t)a * p, S + (size_t)b * p, p);
+            const double k = lagp_oracle_exp(-d / theta);
+            D[a * n + b] = d;
+            K[a * n + b] = (a == b) ? 1.0 + g : k;
+            K1[a * n + b] = (a == b) ? 0.0 : k * d / (theta * theta);
+            K2[a * n + b] = (a == b) ? 0.0
+                : k * (d * d / (theta * theta * theta * theta) - 2.0 * d / (theta * theta * theta));
+        }
+    if (cholesky(K, n, Cm) == 0) {
+        chol_inverse(Cm, n, Ci, Ki);
+        double logdet = 0.0;
+        for (int i = 0; i < n; ++i) logdet = logdet + 2.0 * log(Cm[i * n + i]);
+        for (int i = 0; i < n; ++i) {
+            double t = 0.0;
+            for (int k = 0; k < n; ++k) t = t + Ki[i * n + k] * y[k];
+            al[i] = t;
+        }
+        double psi = 0.0;
+        for (int i = 0; i < n; ++i) psi = psi + y[i] * al[i];
+        const double hn = 0.5 * (double)n;
+        ll = log_gamma_half(n) - hn * log(2.0 * M_PI) - 0.5 * logdet - hn * log(psi / 2.0);
+        if (d1 || d2) {
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < n; ++j) {
+                    double t = 0.0;
+                    for (int k = 0; k < n; ++k) t = t + Ki[i * n + k] * K1[k * n + j];
+                    A[i * n + j] = t;
+                }
+            double tr1 = 0.0, tr2 = 0.0, tr11 = 0.0;
+            for (int i = 0; i < n; ++i) tr1 = tr1 + A[i * n + i];
+            for (int i = 0; i < n; ++i)
+                for (int k = 0; k < n; ++k) tr2 = tr2 + Ki[i * n + k] * K2[k * n + i];
+            for (int i = 0; i < n; ++i)
+                for (int k = 0; k < n; ++k) tr11 = tr11 + A[i * n + k] * A[k * n + i];
+            for (int i = 0; i < n; ++i) {                  /* u = K' alpha */
+                double t = 0.0;
+                for (int k = 0; k < n; ++k) t = t + K1[i * n + k] * al[k];
+                u[i] = t;
+            }
+            double ak1a = 0.0, ak2a = 0.0, uku = 0.0;
+            for (int i = 0; i < n; ++i) ak1a = ak1a + al[i] * u[i];
+            for (int i = 0; i < n; ++i)
+                for (int k = 0; k < n; ++k) ak2a = ak2a + al[i] * K2[i * n + k] * al[k];
+            for (int i = 0; i < n; ++i)
+                for (int k = 0; k < n; ++k) uku = uku + u[i] * Ki[i * n + k] * u[k];
+            const double ps1 = -ak1a;
+            const double ps2 = 2.0 * uku - ak2a;
+            if (d1) *d1 = -0.5 * tr1 - hn * ps1 / psi;
+            if (d2) *d2 = -0.5 * (tr2 - tr11) - hn * (ps2 / psi - (ps1 / psi) * (ps1 / psi));
+        }
+    } else {
+        if (d1) *d1 = NAN;
+        if (d2) *d2 = NAN;
+    }
+    free(D); free(K); free(Cm); free(Ci); free(Ki); free(K1); free(K2); free(A); free(al); free(u);
+    return ll;
+}
+
+/* Safeguarded Newton maximisation of lagp_oracle_loglik over [tmin, tmax]
+   (reading M3).  *iters (may be NULL) receives the iterations taken. */
+double lagp_oracle_mle_theta(const double* S, const double* y, int n, int p, double theta0,
+                             double g, double tmin, double tmax, double tol, int maxit,
+                             int* iters)
+{
+    double a = tmin, b = tmax;
+    double t = theta0 < a ? a : (theta0 > b ? b : theta0);
+    int it = 0;
+    while (it < maxit) {
+        ++it;
+        double d1 = 0.0, d2 = 0.0;
+        const double ll = lagp_oracle_loglik(S, y, n, p, t, g, &d1, &d2);
+        if (!(ll == ll) || !(d1 == d1)) break;
+        if (d1 > 0.0) a = t; else b = t;
+        if (b - a <= tol * t) break;
+        double tn = t - d1 / d2;
+        if (!(d2 < 0.0) || !(tn > a && tn < b)) tn = 0.5 * (a + b);
+        const double step = tn - t;
+        t = tn;
+        if (fabs(step) <= tol * t) break;
+    }
+    if (iters) *iters = it;
+    return t;
+}
+
+/* Resets a location to the empty design at lengthscale theta. */
+static void reset_location(loc_t* L, double theta)
+{
+    L->theta = theta;
+    L->j = 0;
+    memset(L->used, 0, (size_t)L->nc);
+    for (int i = 0; i < L->n * L->n; ++i) L->Kinv[i] = 0.0;
+}
+
+/* Greedy design at L->theta from the empty design (as in one_location). */
+static int build_design(loc_t* L, int search, int nrays)
+{
+    for (int r = 0; r < L->n0; ++r)
+        if (!(add_point(L, r) > 0.0)) return ST_BAD_UPDATE;
+    for (int j = L->n0; j < L->n; ++j) {
+        double gap = 0.0;
+        int ne = 0;
+        int r = (search == 0) ? search_exhaustive(L, &gap) : search_ray(L, nrays, &gap, &ne);
+        if (r < 0 || !(add_point(L, r) > 0.0)) return ST_BAD_UPDATE;
+    }
+    return 0;
+}
+
+/*
+ * One location with local inference for theta (readings M1-M4): stages
+ * designs and estimates, then the predictive equations at the last estimate
+ * on the last design.  K^{-1} at the estimate is rebuilt by the partitioned
+ * update over the design in selection order (R12).
+ */
+static int one_location_mle(const double* X, const double* Y, int64_t N, int p,
+                            const double* lo, const double* hi, const double* x, int n0, int n,
+                            int nc, double theta0, double g, double tmin, double tmax,
+                            int search, int nrays, int stages, double* mean, double* s2,
+                            double* theta_out, int32_t* sel_out)
+{
+    int32_t* cidx = (int32_t*)malloc(sizeof(int32_t) * (size_t)nc);
+    loc_t L;
+    L.p = p; L.nc = nc; L.n0 = n0; L.n = n; L.g = g;
+    L.x = x; L.lo = lo; L.hi = hi;
+    L.cx = (double*)malloc(sizeof(double) * (size_t)nc * p);
+    L.S = (double*)malloc(sizeof(double) * (size_t)n * p);
+    L.Kinv = (double*)calloc((size_t)n * n, sizeof(double));
+    L.kx = (double*)malloc(sizeof(double) * (size_t)n);
+    L.work = (double*)malloc(sizeof(double) * (size_t)(4 * n + 4 * p));
+    L.used = (unsigned char*)calloc((size_t)nc, 1);
+    L.sel = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t* order = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    double* yS = (double*)malloc(sizeof(double) * (size_t)n);
+    int status = 0;
+
+    lagp_oracle_knn(X, N, p, x, nc, cidx, NULL);
+    for (int r = 0; r < nc; ++r)
+        memcpy(L.cx + (size_t)r * p, X + (int64_t)cidx[r] * p, sizeof(double) * p);
+
+    double theta = theta0;
+    for (int s = 0; s < stages && !status; ++s) {
+        reset_location(&L, theta);
+        status = build_design(&L, search, nrays);
+        if (status) break;
+        for (int i = 0; i < n; ++i) yS[i] = Y[cidx[L.sel[i]]];
+        theta = lagp_oracle_mle_theta(L.S, yS, n, p, theta, g, tmin, tmax, 1e-10, 200, NULL);
+    }
+    if (!status) {
+        memcpy(order, L.sel, sizeof(int32_t) * (size_t)n);
+        reset_location(&L, theta);
+        for (int i = 0; i < n && !status; ++i)
+            if (!(add_point(&L, order[i]) > 0.0)) status = ST_BAD_UPDATE;
+    }
+    if (!status) {
+        predict(&L, yS, mean, s2);
+        *theta_out = theta;
+        for (int i = 0; i < n; ++i) sel_out[i] = cidx[L.sel[i]];
+    } else {
+        *mean = NAN;
+        *s2 = NAN;
+        *theta_out = NAN;
+        for (int i = 0; i < n; ++i) sel_out[i] = -1;
+    }
+    free(cidx); free(L.cx); free(L.S); free(L.Kinv); free(L.kx); free(L.work);
+    free(L.used); free(L.sel); free(order); free(yS);
+    return status;
+}
+
+/* Batch driver of one_location_mle over M locations (OpenMP over locations
+   when nthreads != 1); sel_out is [M][n].  Returns the threads used. */
+int lagp_oracle_predict_mle(const double* X, const double* Y, int64_t N, int p,
+                            const double* Xref, int64_t M, int n0, int n, int nc,
+                            double theta0, double g, double tmin, double tmax, int search,
+                            int nrays, int stages, double* mean, double* s2, double* theta_out,
+                            int32_t* sel_out, int32_t* status_out, int nthreads)
+{
+    double* lo = (double*)malloc(sizeof(double) * (size_t)p);
+    double* hi = (double*)malloc(sizeof(double) * (size_t)p);
+    lagp_oracle_bbox(X, N, p, lo, hi);
+    int used_threads = 1;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#endif
+    for (int64_t m = 0; m < M; ++m) {
+#ifdef _OPENMP
+        if (m == 0) used_threads = omp_get_num_threads();
+#endif
+        const int R = nrays > 0 ? nrays : p;
+        status_out[m] = one_location_mle(X, Y, N, p, lo, hi, Xref + m * p, n0, n, nc, theta0,
+                                         g, tmin, tmax, search, R, stages, mean + m, s2 + m,
+                                         theta_out + m, sel_out + m * n);
+    }
+    (void)nthreads;
+    free(lo);
+    free(hi);
+    return used_threads;
+}
