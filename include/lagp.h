@@ -172,6 +172,38 @@ int laGP_knn_noalloc(const double* design, int64_t N, int p, const double* xref,
                      int N_close, int32_t* cand, unsigned* status, void* stream);
 
 /*
+ * Local inference for the lengthscale on given local designs (Sec 5: local
+ * designs are coupled with Newton-like maximisation of the local posterior of
+ * theta; Sec 2.1, Eq. gpk), then the predictive equations (Eq. predgp,
+ * preds2) at the estimate.  Binary64.  For location m the design is the rows
+ * sel[m][0..n-1] of `design`.  theta maximises the marginal likelihood of Eq.
+ * gpk (reference prior on tau^2, flat prior on theta over [tmin, tmax], nugget
+ * g fixed, 1 + g on the diagonal of K) by Newton's method from theta0,
+ * safeguarded by a bracket kept from the sign of the derivative (midpoint
+ * steps where Newton's would leave it or the curvature is not negative), to a
+ * relative step or bracket of 1e-10, 200 iterations at most.  With `sel` the
+ * selected output of laGP_build_and_predict at theta0 this is the first stage
+ * of a local design coupled with local inference; a second stage calls
+ * laGP_build_and_predict again at the estimate.
+ *   design, y   device [N][p], [N] binary64
+ *   xref        device [M][p] binary64
+ *   sel         device [M][n] int32 design indices (each in [0, N))
+ *   n           local design size, 1 <= n <= 64 (n <= N); 1 <= p <= 16
+ *   theta0, g   start (theta0 > 0, clamped to the range) and nugget (g >= 0)
+ *   tmin, tmax  the range, 0 < tmin < tmax
+ *   theta_out, mean, s2  device [M] binary64 out; iters device [M] int32 out or NULL
+ *   status      device unsigned*, cleared by the call; LAGP_STATUS_NUMERIC when
+ *               a location's K is not positive definite at its estimate or an
+ *               index in sel is out of range (that location's outputs are NaN)
+ * Asynchronous on `stream`.  Returns LAGP_OK, LAGP_ERR_INVALID (before any
+ * device work) or LAGP_ERR_CUDA.  No device memory is allocated.
+ */
+int laGP_mle_predict(const double* design, const double* y, int64_t N, int p,
+                     const double* xref, int64_t M, const int32_t* sel, int n, double theta0,
+                     double g, double tmin, double tmax, double* theta_out, double* mean,
+                     double* s2, int32_t* iters, unsigned* status, void* stream);
+
+/*
  * Waits for `stream`, then reads and clears the device status word of the
  * workspace.  *status receives the LAGP_STATUS_* bits.  Returns LAGP_OK when
  * no bit was set, LAGP_ERR_DEVICE when one was, LAGP_ERR_CUDA when the wait

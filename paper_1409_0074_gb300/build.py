@@ -29,6 +29,7 @@ UNITS = {
     "knn_noalloc.cu": [],
     "schedule.cu": [],
     "serve.cu": [],
+    "mle.cu": [],
 }
 
 

@@ -29,7 +29,7 @@ EXPORTED = ("laGP_workspace_bytes", "laGP_build_and_predict", "laGP_knn_workspac
             "laGP_autotune", "laGP_tune_get", "laGP_tune_set", "laGP_plan_create",
             "laGP_plan_launch", "laGP_plan_destroy", "laGP_ctx_design_bytes",
             "laGP_ctx_request_bytes", "laGP_ctx_create", "laGP_ctx_submit", "laGP_ctx_poll",
-            "laGP_ctx_wait", "laGP_ctx_capacity", "laGP_ctx_destroy")
+            "laGP_ctx_wait", "laGP_ctx_capacity", "laGP_ctx_destroy", "laGP_mle_predict")
 
 _lib = None
 
@@ -104,6 +104,9 @@ def load():
     lib.laGP_ctx_capacity.argtypes = [vp, C.POINTER(C.c_size_t), ip]
     lib.laGP_ctx_destroy.restype = i32
     lib.laGP_ctx_destroy.argtypes = [vp]
+    lib.laGP_mle_predict.restype = i32
+    lib.laGP_mle_predict.argtypes = [vp, vp, i64, i32, vp, i64, vp, i32, dbl, dbl, dbl, dbl,
+                                     vp, vp, vp, vp, vp, vp]
     _lib = lib
     return lib
 
@@ -183,6 +186,42 @@ def laGP_knn(design, xref, N_close, cand, workspace, stream=None):
                          N_close, _ptr(cand, torch.int32, M * N_close), _ptr(workspace),
                          workspace.numel() * workspace.element_size(), _stream(stream))
     _check("laGP_knn", rc)
+
+
+def laGP_mle_predict(design, y, xref, sel, theta0, g, tmin, tmax, theta_out, mean, s2,
+                     status, iters=None, stream=None):
+    """Local maximum-likelihood lengthscale on the designs `sel` [M][n] and the
+    predictive equations at it (device tensors; asynchronous on `stream`)."""
+    import torch
+    N, p = design.shape
+    M, n = sel.shape
+    rc = load().laGP_mle_predict(_ptr(design, torch.float64), _ptr(y, torch.float64, N), N, p,
+                                 _ptr(xref, torch.float64, M * p), M, _ptr(sel, torch.int32),
+                                 n, float(theta0), float(g), float(tmin), float(tmax),
+                                 _ptr(theta_out, torch.float64, M), _ptr(mean, torch.float64, M),
+                                 _ptr(s2, torch.float64, M), _ptr(iters, torch.int32, M),
+                                 _ptr(status, torch.int32, 1), _stream(stream))
+    _check("laGP_mle_predict", rc)
+
+
+def mle_predict(design, y, xref, sel, theta0, g, tmin, tmax, stream=None):
+    """Convenience wrapper: allocates the outputs, runs laGP_mle_predict and
+    checks the device status.  Returns a dict of CUDA tensors (theta, mean, s2,
+    iters)."""
+    import torch
+    M = xref.shape[0]
+    dev = design.device
+    out = dict(theta=torch.empty(M, dtype=torch.float64, device=dev),
+               mean=torch.empty(M, dtype=torch.float64, device=dev),
+               s2=torch.empty(M, dtype=torch.float64, device=dev),
+               iters=torch.empty(M, dtype=torch.int32, device=dev))
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    laGP_mle_predict(design, y, xref, sel, theta0, g, tmin, tmax, out["theta"], out["mean"],
+                     out["s2"], st, iters=out["iters"], stream=stream)
+    stv = int(st.cpu()[0])
+    if stv:
+        raise LagpError("laGP_mle_predict (device)", -4, stv)
+    return out
 
 
 def laGP_status(workspace, stream=None):

@@ -91,6 +91,30 @@ def test_invalid_calls_return_before_touching_the_device(lib):
              None, None, None, fake, 1 << 30, None) == 0
 
 
+def test_mle_argument_checks_return_before_touching_the_device(lib):
+    """laGP_mle_predict rejects out-of-range sizes, ranges and a missing status
+    word before any device work (returns -1 without a GPU)."""
+    vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int, C.c_double
+    f = lib.laGP_mle_predict
+    f.restype = C.c_int
+    f.argtypes = [vp, vp, i64, i32, vp, i64, vp, i32, dbl, dbl, dbl, dbl, vp, vp, vp, vp, vp, vp]
+    fake = 4096
+
+    def call(N=1000, p=2, M=10, n=30, theta0=0.1, g=1e-6, tmin=1e-3, tmax=2.0, status=fake):
+        return f(fake, fake, N, p, fake, M, fake, n, theta0, g, tmin, tmax, fake, fake, fake,
+                 None, status, None)
+
+    assert call(n=65) == -1          # n above 64
+    assert call(n=0) == -1
+    assert call(p=17) == -1
+    assert call(N=20) == -1          # n > N
+    assert call(tmin=0.0) == -1
+    assert call(tmax=1e-3) == -1     # tmax <= tmin
+    assert call(theta0=0.0) == -1
+    assert call(g=-1.0) == -1
+    assert call(status=None) == -1
+
+
 def test_host_only_entry_points_of_tuning_plans_and_contexts(lib):
     """Sizes, the launch-choice table and argument checks of the plan and
     serving-context entry points need no device."""
