@@ -137,7 +137,9 @@ int laGP_build_and_predict(const double* design, const double* y, int64_t N, int
  * Step 1 alone (Sec 2.2): the N_close nearest design points of each location,
  * ordered by squared Euclidean distance computed in binary64 as
  * sum_k (X_ik - x_k)^2 (ascending k), ties to the lower index.
- *   cand      device [M][N_close] int32 out
+ *   cand      device [M][N_close] int32 out.  When a location's search ends
+ *             with LAGP_STATUS_CAPACITY or LAGP_STATUS_TIMEOUT, its list may be
+ *             incomplete; the missing ranks repeat an index of the design.
  *   workspace sized by laGP_knn_workspace_bytes(N, p, M, N_close)
  */
 size_t laGP_knn_workspace_bytes(int64_t N, int p, int64_t M, int N_close);

@@ -462,8 +462,11 @@ knn_rank(const double* __restrict__ X, int p, const double* __restrict__ xref, i
     }
   }
   if (c < nc && threadIdx.x == 0) atomicOr(status, LAGP_DEV_KNN_OVERFLOW);
+  // ranks this location lacks (a flagged overflow or timeout) repeat a valid
+  // index, so that the design kernels never read outside the design
+  const int32_t fill = c > 0 ? idx[0] : 0;
   for (int r = threadIdx.x; r < nc_max; r += blockDim.x)
-    cand[q * nc_max + r] = (r < nc && r < c) ? idx[r] : -1;
+    cand[q * nc_max + r] = (r < nc) ? (r < c ? idx[r] : fill) : -1;
 }
 
 // ---------------------------------------------------------------------------
