@@ -96,6 +96,26 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
+def shard(M_total, rank, world):
+    """Contiguous block [lo, hi) of the job's M_total locations that `rank`
+    predicts; the blocks of ranks 0..world-1 are disjoint, cover the job and
+    follow rank order."""
+    per, extra = divmod(M_total, world)
+    lo = rank * per + min(rank, extra)
+    return lo, lo + per + (1 if rank < extra else 0)
+
+
+def rank_workload(M, N, rank, world):
+    """The workload of one rank (weak scaling, M locations per rank): every
+    rank draws the same design, responses and job-wide location set (seed 0,
+    M * world locations) and keeps its own block of them."""
+    from paper_1409_0074_gb300 import workloads as W
+    w = W.large_8d(M=M * world, N=N)
+    lo, hi = shard(w.M, rank, world)
+    w.Xref, w.Ytrue, w.M = w.Xref[lo:hi], w.Ytrue[lo:hi], hi - lo
+    return w
+
+
 def whole_job_rate(units_per_rank, steps, ms, world):
     """Units per second of the whole job: all ranks' units over the slowest
     rank's time.  Returns (rate, slowest ms)."""
@@ -204,17 +224,35 @@ def design32_traffic_per_location():
                            "traffic_bytes_per_location")
 
 
-def kernel_flops(name, w, nevals_sum_j):
-    """Algorithmic FLOPs of one launch's worth of work (see the design notes):
-    kNN 3 N p per location; a ray evaluation at design size j costs
-    j^2 + j (triangular matvec) + 4 j (two dots) + (3p + 2) j (correlations);
-    the exhaustive FP32 scoring step j^2 + j + 4j per candidate."""
+def kernel_flops(name, w, ev):
+    """Algorithmic FLOPs of one launch's worth of work, and the FLOPs the
+    kernel's own arithmetic form executes (None where they are the same).
+      kNN: 3 N p per location (subtract, multiply, add per coordinate).
+      Ray search: an ALC evaluation at design size j counts 2 j^2 (the matvec
+      with K_j^{-1}) + (3p + 4) j (correlation distances, the two dots), and
+      each greedy step adds the snap's N' x 3p.  The FP32 kernel forms the
+      quadratic through the triangular L_j^{-1}: j^2 + j + 4 j + (3p + 2) j per
+      evaluation.
+    ev: sum over the launch's evaluations of j (s1) and of j^2 (s2), and its
+    greedy steps."""
     if name == "knn_stream":
-        return 3.0 * w["N"] * w["p"] * w["M_launch"]
-    if name in ("design32_ray", "ray32"):
-        s1, s2 = nevals_sum_j      # sum over evaluations of j and of j^2
-        return s2 + (5 + 3 * w["p"] + 2) * s1
-    return None
+        return 3.0 * w["N"] * w["p"] * w["M_launch"], None
+    if name in ("design32_ray", "ray32", "design64_ray"):
+        p, nc = w["p"], w["nc"]
+        snap = ev["steps"] * nc * 3 * p
+        algo = 2 * ev["s2"] + (3 * p + 4) * ev["s1"] + snap
+        tri = ev["s2"] + (5 + 3 * p + 2) * ev["s1"] + snap
+        return algo, (tri if name != "design64_ray" else None)
+    if name == "design64_exhaustive":
+        # per step and unselected candidate: the full ALC in the explicit form
+        p, nc, n0, n = w["p"], w["nc"], w["n0"], w["n"]
+        per_loc = sum((nc - j) * (2 * j * j + (3 * p + 4) * j) for j in range(n0, n))
+        return per_loc * w["M_launch"], None
+    if name == "exh_tc":
+        nc, n0, n = w["nc"], w["n0"], w["n"]
+        per_loc = sum(nc * (2 * j * j + 4 * j) for j in range(n0, n))
+        return per_loc * w["M_launch"], None
+    return None, None
 
 
 def kernel_bytes(name, w):
@@ -229,13 +267,57 @@ def kernel_bytes(name, w):
     return per_loc * w["M_launch"]
 
 
+def eval_sums(nev, n0):
+    """Sums over a launch's ray evaluations of j and j^2 (nev: [M][n - n0]
+    evaluations per greedy step) and its greedy steps."""
+    js = np.arange(n0, n0 + nev.shape[1], dtype=np.float64)
+    return {"s1": float((nev * js[None, :]).sum()), "s2": float((nev * js[None, :] ** 2).sum()),
+            "steps": float(nev.shape[0] * nev.shape[1])}
+
+
+def roofline(name, tot_ms, launches, w, M_launch, ev=None, traffic_ok=False):
+    """Roofline entry of one kernel from its profiled time: achieved work per
+    launch over the average launch time, against the bound's peak.  ev: the
+    evaluation sums of one launch (eval_sums), for the ray kernels."""
+    per_launch_ms = tot_ms / launches
+    shape = dict(N=w.N, p=w.p, n0=w.n0, n=w.n, nc=w.nc, PP=(w.p + 3) // 4 * 4,
+                 M_launch=M_launch)
+    nbytes = kernel_bytes(name, shape)
+    if nbytes is not None:
+        achieved = nbytes / (per_launch_ms / 1e3) / 1e9
+        peak, src = hbm_peak()
+        tpl = design32_traffic_per_location() if (w.n == 50 and w.nc == 1000 and w.p == 8
+                                                   and w.N == 1_000_000) else None
+        return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None if tpl is None else tpl * M_launch,
+                "peak_source": src, "launch_ms": per_launch_ms}
+    algo, executed = kernel_flops(name, shape, ev)
+    if algo is None:
+        return None
+    fp64 = name.startswith("design64")
+    peak = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
+    achieved = algo / (per_launch_ms / 1e3) / 1e12
+    out = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
+           "unit": "TFLOP/s", "frac": achieved / peak,
+           "traffic": ray32_traffic() if (name == "ray32" and traffic_ok) else None,
+           "peak_source": ("GB300 FP64 rate, nominal" if fp64 else
+                           "152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (nominal)"),
+           "flop_count": ("2j^2 + (3p+4)j per ALC evaluation + N' x 3p per greedy step"
+                          if "ray" in name else "per-step algorithmic count, see the design notes"),
+           "launch_ms": per_launch_ms}
+    if executed is not None:
+        out["achieved_executed_form"] = executed / (per_launch_ms / 1e3) / 1e12
+        out["frac_executed_form"] = out["achieved_executed_form"] / peak
+    return out
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_1409_0074_gb300 import lagp
-    from paper_1409_0074_gb300 import workloads as W
 
     dev = torch.device("cuda", torch.cuda.current_device())
-    w = W.large_8d(M=args.M, N=args.N, seed=rank)
+    w = rank_workload(args.M, args.N, rank, world)
     N, p, M = w.N, w.p, w.M
     s, pr = lagp.SEARCH[args.search], lagp.PRECISION[args.precision]
     R = w.nrays
@@ -284,34 +366,10 @@ def run_ours(args, rank, world):
     trace = lagp.predict(X, Y, Xr, w.n0, w.n, w.nc, w.theta, w.g, search=args.search,
                          nrays=R, precision=args.precision, want_trace=True)
     nev = trace["nevals"].cpu().numpy()[:, : w.n - w.n0].astype(np.float64)
-    js = np.arange(w.n0, w.n, dtype=np.float64)
-    sum_j = float((nev * js[None, :]).sum())
-    sum_j2 = float((nev * js[None, :] ** 2).sum())
-    chunks = launches // args.steps
-    work = kernel_flops(name, dict(N=N, p=p, M_launch=M / max(chunks, 1)),
-                        (sum_j / max(chunks, 1), sum_j2 / max(chunks, 1)))
-    roof = None
-    nbytes = kernel_bytes(name, dict(n=w.n, nc=w.nc, PP=(p + 3) // 4 * 4,
-                                     M_launch=M / max(chunks, 1)))
-    if nbytes is not None:
-        per_launch_ms = tot_ms / launches
-        achieved = nbytes / (per_launch_ms / 1e3) / 1e9
-        peak, src = hbm_peak()
-        tpl = design32_traffic_per_location() if (w.n == 50 and w.nc == 1000 and w.p == 8
-                                                   and w.N == 1_000_000) else None
-        roof = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None if tpl is None else tpl * M / max(chunks, 1),
-                "peak_source": src, "launch_ms": per_launch_ms}
-    elif work is not None:
-        per_launch_ms = tot_ms / launches
-        achieved = work / (per_launch_ms / 1e3) / 1e12
-        traffic = ray32_traffic() if (name == "ray32" and w.M == 100_000 and w.N == 1_000_000
-                                      and chunks == 1) else None
-        roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz",
-                "launch_ms": per_launch_ms}
+    chunks = max(launches // args.steps, 1)
+    ev = {k: v / chunks for k, v in eval_sums(nev, w.n0).items()}
+    roof = roofline(name, tot_ms, launches, w, M / chunks, ev,
+                    traffic_ok=(w.M == 100_000 and w.N == 1_000_000 and chunks == 1))
     kernels = {k: {"ms_per_step": v[0] / args.steps, "launches": v[1],
                    "share": v[0] / sum(x[0] for x in prof.values())} for k, v in prof.items()}
     mean_evals = float(nev.sum(axis=1).mean() / (w.n - w.n0))
@@ -351,7 +409,8 @@ def run_e2e(args, w):
 
 
 def run_extra(args, w, tensors, search, precision, M, steps=2):
-    """Locations/sec of another search/precision form on the first M locations."""
+    """Locations/sec of another search/precision form on the first M
+    locations, with the roofline of its dominant kernel."""
     import torch
     from paper_1409_0074_gb300 import lagp
     X, Y, Xr = tensors
@@ -361,19 +420,34 @@ def run_extra(args, w, tensors, search, precision, M, steps=2):
     ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
     mean = torch.empty(M, dtype=torch.float64, device="cuda")
     s2 = torch.empty(M, dtype=torch.float64, device="cuda")
+    nev = torch.zeros((M, w.n), dtype=torch.int32, device="cuda") if search == "ray" else None
     go = lambda: lagp.laGP_build_and_predict(X, Y, Xr, w.n0, w.n, w.nc, w.theta, w.g, s,
-                                             w.nrays, pr, mean, s2, ws)
+                                             w.nrays, pr, mean, s2, ws, nevals=nev)
     go()
     torch.cuda.synchronize()
+    lagp.laGP_profile(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(steps):
         go()
     e1.record()
     torch.cuda.synchronize()
+    lagp.laGP_profile(False)
+    prof = lagp.laGP_profile_read()
+    rc, st = lagp.laGP_status(ws)
+    if rc != 0:
+        raise RuntimeError("device status %d in the %s %s form" % (st, search, precision))
+    name, (tot_ms, launches) = max(prof.items(), key=lambda kv: kv[1][0])
+    chunks = max(launches // steps, 1)
+    ev = None
+    if nev is not None:
+        nv = nev.cpu().numpy()[:, : w.n - w.n0].astype(np.float64)
+        ev = {k: v / chunks for k, v in eval_sums(nv, w.n0).items()}
     rmse = float(np.sqrt(np.mean((mean.cpu().numpy() - w.Ytrue[:M]) ** 2)))
     return {"locations_per_s": M * steps / (e0.elapsed_time(e1) / 1e3), "locations": M,
-            "rmse": rmse}
+            "rmse": rmse, "roofline": roofline(name, tot_ms, launches, w, M / chunks, ev),
+            "kernels": {k: {"ms_per_step": v[0] / steps, "launches": v[1]}
+                        for k, v in prof.items()}}
 
 
 def run_batching(args, steps=3):
@@ -485,7 +559,7 @@ def run_serving(args, rates=(25.0, 50.0, 100.0)):
     return out
 
 
-def run_cpu_baseline(args, w, search, sample=None):
+def run_cpu_baseline(args, w, search, sample=None, one_core=False):
     """The FP64 oracle as it stands, OpenMP over locations on the host cores."""
     import oracle
     cores = os.cpu_count() or 1
@@ -495,9 +569,18 @@ def run_cpu_baseline(args, w, search, sample=None):
     r = oracle.predict(w.X, w.Y, w.Xref[:S], w.n0, w.n, w.nc, w.theta, w.g, search,
                        nrays=w.nrays, nthreads=0)
     dt = time.perf_counter() - t0
-    return {"value": S / dt, "unit": "locations/s", "cores": int(r["threads"]), "kind": "oracle",
-            "sample": "first %d of the %d locations, %s search, FP64" % (S, w.M, search),
-            "seconds": dt}
+    out = {"value": S / dt, "unit": "locations/s", "cores": int(r["threads"]), "kind": "oracle",
+           "sample": "first %d of the %d locations, %s search, FP64" % (S, w.M, search),
+           "seconds": dt}
+    if one_core:
+        S1 = min(max(4, S // (4 * cores)), w.M)
+        t0 = time.perf_counter()
+        oracle.predict(w.X, w.Y, w.Xref[:S1], w.n0, w.n, w.nc, w.theta, w.g, search,
+                       nrays=w.nrays, nthreads=1)
+        dt1 = time.perf_counter() - t0
+        out["one_core"] = {"value": S1 / dt1, "unit": "locations/s", "cores": 1,
+                           "sample": "first %d locations" % S1, "seconds": dt1}
+    return out
 
 
 def base_line(args, world, value, ms, w):
@@ -520,8 +603,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        from paper_1409_0074_gb300 import workloads as W
-        w = W.large_8d(M=args.M, N=args.N)
+        w = rank_workload(args.M, args.N, 0, 1)
         cores = os.cpu_count() or 1
         S = args.cpu_sample or 8 * cores
         if args.warmup > 0:   # one short untimed pass (page-in, thread start-up)
@@ -564,7 +646,7 @@ def main():
         if not args.no_serving:
             line["serving_form"] = run_serving(args)
         if not args.no_cpu:
-            line["cpu_baseline"] = run_cpu_baseline(args, w, args.search)
+            line["cpu_baseline"] = run_cpu_baseline(args, w, args.search, one_core=True)
     else:
         line["e2e"] = None
     if rank == 0:

@@ -157,14 +157,16 @@ int laGP_knn(const double* design, int64_t N, int p, const double* xref, int64_t
  *
  *   design, N, p, xref, M, N_close, cand: as in laGP_knn (device pointers)
  *   status    device unsigned* or NULL: receives the LAGP_STATUS_* bits of
- *             this call once the stream reaches the end of it
+ *             this call once the stream reaches the end of it (0 when M = 0)
  *   stream    cudaStream_t
  * Limits: the scratch needed, laGP_knn_workspace_bytes(N, p, M, N_close),
  * must not exceed LAGP_KNN_NOALLOC_SCRATCH_BYTES (64 MiB); larger requests
  * return LAGP_ERR_WORKSPACE before any device work.  Every GPU that loads the
  * library holds that array until the process exits.
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  All calls
+ * device current); make that first call before any stream capture.  A call
+ * that finds the device under a new context (after cudaDeviceReset) looks the
+ * address up again, so it too belongs outside a stream capture.  All calls
  * share the one array and each overwrites it: calls that overlap on the GPU
  * (concurrent streams, threads or devices sharing a context) race, so
  * serialise them.  No device memory is allocated or freed.

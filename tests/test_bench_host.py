@@ -75,3 +75,35 @@ def test_reference_arm_prints_the_contract_line():
     assert d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["e2e"]["value"] == d["value"]
+
+
+def test_ray_flops_follow_the_algorithmic_count():
+    """A ray launch counts 2 j^2 + (3p + 4) j per ALC evaluation at design size
+    j and N' x 3p per greedy step (the snap), summed here evaluation by
+    evaluation; the executed triangular form j^2 + j + 4 j + (3p + 2) j is the
+    second figure."""
+    import numpy as np
+    nev = np.array([[3, 5, 0], [4, 1, 2]], dtype=np.float64)   # 2 locations, j = 2, 3, 4
+    n0, p, nc = 2, 3, 20
+    ev = bench.eval_sums(nev, n0)
+    want_algo = want_tri = 0
+    for row in nev:
+        for j, e in zip((2, 3, 4), row):
+            want_algo += e * (2 * j * j + (3 * p + 4) * j) + nc * 3 * p
+            want_tri += e * (j * j + j + 4 * j + (3 * p + 2) * j) + nc * 3 * p
+    shape = dict(N=100, p=p, n0=n0, n=5, nc=nc, PP=4, M_launch=2)
+    algo, tri = bench.kernel_flops("ray32", shape, ev)
+    assert algo == want_algo and tri == want_tri
+    algo64, tri64 = bench.kernel_flops("design64_ray", shape, ev)
+    assert algo64 == want_algo and tri64 is None
+
+
+def test_exhaustive_fp64_flops_by_brute_force():
+    n0, n, nc, p = 2, 5, 9, 2
+    want = 0
+    for j in range(n0, n):
+        for _cand in range(nc - j):
+            want += 2 * j * j + (3 * p + 4) * j
+    got, _ = bench.kernel_flops("design64_exhaustive",
+                                dict(N=50, p=p, n0=n0, n=n, nc=nc, PP=4, M_launch=3), None)
+    assert got == 3 * want

@@ -62,6 +62,20 @@ def test_noalloc_knn_matches_workspace_entry_twice(lib):
         np.testing.assert_array_equal(cand.cpu().numpy(), expect)
 
 
+def test_noalloc_empty_request_clears_the_status_word(lib):
+    """M = 0 enqueues no search, yet the caller's status word reports the call."""
+    import torch
+    fn = lib.load().laGP_knn_noalloc
+    X = torch.from_numpy(np.random.default_rng(3).random((500, 3))).cuda()
+    status = torch.full((1,), 12345, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    rc = fn(X.data_ptr(), 500, 3, X.data_ptr(), 0, 50, None, status.data_ptr(),
+            stream.cuda_stream)
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+
+
 def test_noalloc_rejects_requests_beyond_its_scratch(lib):
     fn = lib.load().laGP_knn_noalloc
     need = lib.laGP_knn_workspace_bytes(4_000_000, 8, 1000, 1000)
