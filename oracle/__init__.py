@@ -17,7 +17,9 @@ only piecewise (round-robin offsets, segments, Brent minima, snapping): the
 paper prints no worked ray example, so whole ray designs are "parity unpinned"
 beyond those pieces.
 """
+import contextlib
 import ctypes as C
+
 import numpy as np
 
 from . import build as _build
@@ -29,46 +31,73 @@ _F1 = C.CFUNCTYPE(C.c_double, C.c_double, C.c_void_p)
 def lib():
     global _lib
     if _lib is None:
-        _lib = C.CDLL(_build.build())
-        dp, ip = C.POINTER(C.c_double), C.POINTER(C.c_int32)
-        _lib.lagp_oracle_exp.restype = C.c_double
-        _lib.lagp_oracle_exp.argtypes = [C.c_double]
-        _lib.lagp_oracle_sqdist.restype = C.c_double
-        _lib.lagp_oracle_sqdist.argtypes = [dp, dp, C.c_int]
-        _lib.lagp_oracle_knn.restype = C.c_int
-        _lib.lagp_oracle_knn.argtypes = [dp, C.c_int64, C.c_int, dp, C.c_int, ip, dp]
-        _lib.lagp_oracle_update.restype = C.c_double
-        _lib.lagp_oracle_update.argtypes = [dp, C.c_int, C.c_int, dp, C.c_double, dp]
-        _lib.lagp_oracle_alc.restype = C.c_double
-        _lib.lagp_oracle_alc.argtypes = [dp, C.c_int, C.c_int, dp, C.c_int, dp, dp, dp,
-                                         C.c_double, C.c_double, dp, dp, dp]
-        _lib.lagp_oracle_brent.restype = C.c_double
-        _lib.lagp_oracle_brent.argtypes = [_F1, C.c_void_p, C.c_double, C.c_double,
-                                           C.c_double, C.c_int, dp, C.POINTER(C.c_int), dp]
-        _lib.lagp_oracle_ray_k.restype = C.c_int
-        _lib.lagp_oracle_ray_k.argtypes = [C.c_int, C.c_int]
-        _lib.lagp_oracle_ray_segment.restype = C.c_double
-        _lib.lagp_oracle_ray_segment.argtypes = [dp, dp, dp, dp, C.c_int, dp]
-        _lib.lagp_oracle_bbox.restype = None
-        _lib.lagp_oracle_bbox.argtypes = [dp, C.c_int64, C.c_int, dp, dp]
-        _lib.lagp_oracle_predict.restype = C.c_int
-        _lib.lagp_oracle_predict.argtypes = [
-            dp, dp, C.c_int64, C.c_int, dp, C.c_int64, C.c_int, C.c_int, C.c_int,
-            ip, ip, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
-            dp, dp, ip, dp, ip, ip, C.c_int]
-        _lib.lagp_oracle_loglik.restype = C.c_double
-        _lib.lagp_oracle_loglik.argtypes = [dp, dp, C.c_int, C.c_int, C.c_double, C.c_double,
-                                            dp, dp]
-        _lib.lagp_oracle_mle_theta.restype = C.c_double
-        _lib.lagp_oracle_mle_theta.argtypes = [dp, dp, C.c_int, C.c_int, C.c_double,
-                                               C.c_double, C.c_double, C.c_double,
-                                               C.c_double, C.c_int, C.POINTER(C.c_int)]
-        _lib.lagp_oracle_predict_mle.restype = C.c_int
-        _lib.lagp_oracle_predict_mle.argtypes = [
-            dp, dp, C.c_int64, C.c_int, dp, C.c_int64, C.c_int, C.c_int, C.c_int,
-            C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int,
-            dp, dp, dp, ip, ip, C.c_int]
+        _lib = _configure(C.CDLL(_build.build()))
     return _lib
+
+
+@contextlib.contextmanager
+def library(path):
+    """Route every call of this module to another build of the oracle while
+    the block runs (the planted-mistake tests compile altered copies)."""
+    global _lib
+    saved = _lib
+    _lib = _configure(C.CDLL(path))
+    try:
+        yield
+    finally:
+        _lib = saved
+
+
+def set_jitter(seed):
+    """Rounding-noise probe: with seed != 0 every correlation value is
+    multiplied by 1 +- 2^-52 (a counter-based choice per location and call);
+    seed 0 switches it off."""
+    lib().lagp_oracle_set_jitter(C.c_uint64(int(seed)))
+
+
+def _configure(L):
+    """Declares the C signatures on a loaded oracle library; returns it."""
+    dp, ip = C.POINTER(C.c_double), C.POINTER(C.c_int32)
+    L.lagp_oracle_set_jitter.restype = None
+    L.lagp_oracle_set_jitter.argtypes = [C.c_uint64]
+    L.lagp_oracle_exp.restype = C.c_double
+    L.lagp_oracle_exp.argtypes = [C.c_double]
+    L.lagp_oracle_sqdist.restype = C.c_double
+    L.lagp_oracle_sqdist.argtypes = [dp, dp, C.c_int]
+    L.lagp_oracle_knn.restype = C.c_int
+    L.lagp_oracle_knn.argtypes = [dp, C.c_int64, C.c_int, dp, C.c_int, ip, dp]
+    L.lagp_oracle_update.restype = C.c_double
+    L.lagp_oracle_update.argtypes = [dp, C.c_int, C.c_int, dp, C.c_double, dp]
+    L.lagp_oracle_alc.restype = C.c_double
+    L.lagp_oracle_alc.argtypes = [dp, C.c_int, C.c_int, dp, C.c_int, dp, dp, dp,
+                                     C.c_double, C.c_double, dp, dp, dp]
+    L.lagp_oracle_brent.restype = C.c_double
+    L.lagp_oracle_brent.argtypes = [_F1, C.c_void_p, C.c_double, C.c_double,
+                                       C.c_double, C.c_int, dp, C.POINTER(C.c_int), dp]
+    L.lagp_oracle_ray_k.restype = C.c_int
+    L.lagp_oracle_ray_k.argtypes = [C.c_int, C.c_int]
+    L.lagp_oracle_ray_segment.restype = C.c_double
+    L.lagp_oracle_ray_segment.argtypes = [dp, dp, dp, dp, C.c_int, dp]
+    L.lagp_oracle_bbox.restype = None
+    L.lagp_oracle_bbox.argtypes = [dp, C.c_int64, C.c_int, dp, dp]
+    L.lagp_oracle_predict.restype = C.c_int
+    L.lagp_oracle_predict.argtypes = [
+        dp, dp, C.c_int64, C.c_int, dp, C.c_int64, C.c_int, C.c_int, C.c_int,
+        ip, ip, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
+        dp, dp, ip, dp, ip, ip, C.c_int]
+    L.lagp_oracle_loglik.restype = C.c_double
+    L.lagp_oracle_loglik.argtypes = [dp, dp, C.c_int, C.c_int, C.c_double, C.c_double,
+                                        dp, dp]
+    L.lagp_oracle_mle_theta.restype = C.c_double
+    L.lagp_oracle_mle_theta.argtypes = [dp, dp, C.c_int, C.c_int, C.c_double,
+                                           C.c_double, C.c_double, C.c_double,
+                                           C.c_double, C.c_int, C.POINTER(C.c_int)]
+    L.lagp_oracle_predict_mle.restype = C.c_int
+    L.lagp_oracle_predict_mle.argtypes = [
+        dp, dp, C.c_int64, C.c_int, dp, C.c_int64, C.c_int, C.c_int, C.c_int,
+        C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int,
+        dp, dp, dp, ip, ip, C.c_int]
+    return L
 
 
 def _d(a):

@@ -94,10 +94,43 @@ double lagp_oracle_sqdist(const double* a, const double* b, int p)
     return acc;
 }
 
+/* ------------------------------------------------------------------------- */
+/* Rounding-noise probe ("ulp jitter").  When a seed is set, every correlation */
+/* value below is multiplied by 1 + 2^-52 or 1 - 2^-52, chosen by a counter-   */
+/* based generator (SplitMix64 of Steele, Lea & Flood 2014, applied to the     */
+/* seed, the location's index and the call count), so that repeated runs with */
+/* different seeds show how far rounding alone can move the results.  Seed 0  */
+/* (the default) leaves the oracle exact as described above.                  */
+/* ------------------------------------------------------------------------- */
+static uint64_t g_jitter_seed = 0;
+static __thread uint64_t t_jitter_key = 0;
+static __thread uint64_t t_jitter_ctr = 0;
+
+static uint64_t splitmix64(uint64_t z)
+{
+    z += 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+void lagp_oracle_set_jitter(uint64_t seed) { g_jitter_seed = seed; }
+
+static void jitter_location(int64_t m)
+{
+    t_jitter_key = splitmix64(g_jitter_seed ^ splitmix64((uint64_t)m));
+    t_jitter_ctr = 0;
+}
+
 /* Isotropic Gaussian correlation (Sec 2.1): exp(-||a-b||^2 / theta). */
 static double corr(const double* a, const double* b, int p, double theta)
 {
-    return lagp_oracle_exp(-(lagp_oracle_sqdist(a, b, p) / theta));
+    double k = lagp_oracle_exp(-(lagp_oracle_sqdist(a, b, p) / theta));
+    if (g_jitter_seed) {
+        uint64_t h = splitmix64(t_jitter_key + t_jitter_ctr++);
+        k = k * ((h & 1) ? (1.0 + 0x1p-52) : (1.0 - 0x1p-52));
+    }
+    return k;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -627,6 +660,7 @@ int lagp_oracle_predict(const double* X, const double* Y, int64_t N, int p,
         int nm = n_arr ? n_arr[m] : n;
         int ncm = nc_arr ? nc_arr[m] : nc;
         int R = nrays > 0 ? nrays : p;
+        jitter_location(m);
         for (int i = 0; i < n_stride; ++i) {
             sel_out[m * n_stride + i] = -1;
             gap_out[m * n_stride + i] = 0.0;
