@@ -245,3 +245,30 @@ def test_each_planted_gap_mistake_fails_a_pin(name):
                 except AssertionError:
                     failed.append(check.__name__)
         assert failed, "planted mistake '%s' passed every gap pin" % name
+
+
+# --- the rounding-noise probe ----------------------------------------------------
+
+def test_jitter_probe_is_deterministic_and_off_by_default():
+    """Seed 0 leaves the oracle exact; a seed gives the same results whatever
+    the thread count; the perturbation is rounding-sized on a well-conditioned
+    case and different seeds perturb differently."""
+    w = W.small(N=500, p=2, M=6, n0=4, n=12, nc=50, theta=0.01, g=1e-3, seed=23)
+    run = lambda nt=1: oracle.predict(w.X, w.Y, w.Xref, w.n0, w.n, w.nc, w.theta, w.g,
+                                      "exhaustive", nthreads=nt)
+    exact = run()
+    try:
+        oracle.set_jitter(1)
+        a1, a4 = run(1), run(4)
+        oracle.set_jitter(2)
+        b = run()
+    finally:
+        oracle.set_jitter(0)
+    again = run()
+    for k in ("mean", "s2", "selected", "gap"):
+        np.testing.assert_array_equal(again[k], exact[k])
+        np.testing.assert_array_equal(a1[k], a4[k])
+    np.testing.assert_array_equal(a1["selected"], exact["selected"])
+    rel = np.abs(a1["mean"] - exact["mean"]) / np.abs(exact["mean"])
+    assert 0 < rel.max() < 1e-11
+    assert np.any(a1["mean"] != b["mean"])
