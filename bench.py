@@ -450,6 +450,101 @@ def run_extra(args, w, tensors, search, precision, M, steps=2):
                         for k, v in prof.items()}}
 
 
+def run_nrays_sweep(args, w, tensors, M=20_000, steps=2):
+    """Rays per step from 1 to p on the 8-d workload (the paper's fidelity knob,
+    Sec 5.4): locations/s and RMSE of the FP32-scoring ray search per count,
+    on the first M locations."""
+    import torch
+    from paper_1409_0074_gb300 import lagp
+    X, Y, Xr = tensors
+    M = min(M, w.M)
+    Xr = Xr[:M].contiguous()
+    out = {"workload": w.name, "locations": M, "precision": "fp32 scoring", "rays": []}
+    mean = torch.empty(M, dtype=torch.float64, device="cuda")
+    s2 = torch.empty(M, dtype=torch.float64, device="cuda")
+    for R in range(1, w.p + 1):
+        wsb = lagp.laGP_workspace_bytes(w.N, w.p, M, w.n, w.nc, R, lagp.LAGP_RAY,
+                                        lagp.LAGP_FP32_SCORE)
+        ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+        go = lambda: lagp.laGP_build_and_predict(X, Y, Xr, w.n0, w.n, w.nc, w.theta, w.g,
+                                                 lagp.LAGP_RAY, R, lagp.LAGP_FP32_SCORE, mean,
+                                                 s2, ws)
+        go()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            go()
+        e1.record()
+        torch.cuda.synchronize()
+        rc, st = lagp.laGP_status(ws)
+        if rc != 0:
+            raise RuntimeError("device status %d in the nrays sweep" % st)
+        rmse = float(np.sqrt(np.mean((mean.cpu().numpy() - w.Ytrue[:M]) ** 2)))
+        out["rays"].append({"nrays": R, "locations_per_s": M * steps / (e0.elapsed_time(e1) / 1e3),
+                            "rmse": rmse})
+        del ws
+    return out
+
+
+def run_paper_2d(args, steps=2):
+    """The 2-d experiment of Sec 5.1 (201 x 201 grid design on [-2, 2]^2, the
+    99 x 99 predictive grid, n = 50, N' = 1000, one ray): locations/s and RMSE
+    of each search and arithmetic form at theta0 = 0.5, then local inference
+    for theta on the FP64 designs (one stage, laGP_mle_predict) and its RMSE.
+    The paper's Table 1 RMSE (0.0009 ray, 0.0010 exhaustive, one stage) is
+    context: its nugget and theta start are not stated."""
+    import torch
+    from paper_1409_0074_gb300 import lagp
+    from paper_1409_0074_gb300 import workloads as W
+    w = W.paper_2d()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    X, Y, Xr = (torch.from_numpy(a).to(dev) for a in (w.X, w.Y, w.Xref))
+    out = {"workload": w.name, "N": w.N, "M": w.M, "n": w.n, "N_close": w.nc, "nrays": 1,
+           "theta0": w.theta, "g": w.g, "forms": {}}
+    rmse = lambda t: float(np.sqrt(np.mean((t.cpu().numpy() - w.Ytrue) ** 2)))
+    for search in ("ray", "exhaustive"):
+        for prec in ("fp32", "fp64"):
+            s, pr = lagp.SEARCH[search], lagp.PRECISION[prec]
+            wsb = lagp.laGP_workspace_bytes(w.N, w.p, w.M, w.n, w.nc, 1, s, pr)
+            ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+            mean = torch.empty(w.M, dtype=torch.float64, device=dev)
+            s2 = torch.empty(w.M, dtype=torch.float64, device=dev)
+            sel = torch.empty((w.M, w.n), dtype=torch.int32, device=dev)
+            go = lambda: lagp.laGP_build_and_predict(X, Y, Xr, w.n0, w.n, w.nc, w.theta, w.g, s,
+                                                     1, pr, mean, s2, ws, selected=sel)
+            go()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(steps):
+                go()
+            e1.record()
+            torch.cuda.synchronize()
+            rc, st = lagp.laGP_status(ws)
+            if rc != 0:
+                raise RuntimeError("device status %d in the 2-d form" % st)
+            f = {"locations_per_s": w.M * steps / (e0.elapsed_time(e1) / 1e3),
+                 "rmse_theta0": rmse(mean)}
+            if prec == "fp64":
+                th = torch.empty(w.M, dtype=torch.float64, device=dev)
+                m2 = torch.empty(w.M, dtype=torch.float64, device=dev)
+                v2 = torch.empty(w.M, dtype=torch.float64, device=dev)
+                stt = torch.zeros(1, dtype=torch.int32, device=dev)
+                e0.record()
+                lagp.laGP_mle_predict(X, Y, Xr, sel, w.theta, w.g, 1e-3, 10.0, th, m2, v2, stt)
+                e1.record()
+                torch.cuda.synchronize()
+                f["mle_stage1"] = {"rmse": rmse(m2), "ms": e0.elapsed_time(e1),
+                                   "theta_median": float(th.median().item()),
+                                   "status": int(stt.item())}
+            out["forms"]["%s_%s" % (search, prec)] = f
+            del ws
+    out["paper_table1_rmse_context"] = {"ray_n50_stage1": 0.0009, "ext_n50_stage1": 0.0010,
+                                        "nn_n50": 0.0023}
+    return out
+
+
 def run_batching(args, steps=3):
     """Batching form: N = 1e6, p = 8, 50,000 locations with n ~ U{20..100} and
     N' ~ U{300..2000}; the launch choices autotuned on the first 10,000
@@ -502,60 +597,96 @@ def run_batching(args, steps=3):
     return out
 
 
-def run_serving(args, rates=(25.0, 50.0, 100.0)):
+def serve_curve(ctx, w, rates, seconds, rng, max_batch=4096, slots=8, max_requests=None):
+    """Poisson request streams at each rate through one continuous-batching
+    server over the context: p50 / p99 latency (arrival to results in host
+    memory), the locations/s the stream achieved and the RMSE of the served
+    predictions against the true response."""
+    from paper_1409_0074_gb300.serve import (CtxBackend, Server, latency_summary,
+                                             poisson_requests, run_stream)
+    out = []
+    for rate in rates:
+        count = int(rate * seconds)
+        if max_requests:
+            count = min(count, max_requests)
+        reqs = poisson_requests(rng, rate, max(count, 4), w.p)
+        srv = Server(CtxBackend(ctx, max_batch, slots), max_batch)
+        wall = run_stream(srv, reqs)
+        summ = latency_summary(reqs, wall)
+        offered = sum(r.xref.shape[0] for r in reqs) / max(reqs[-1].arrival - reqs[0].arrival,
+                                                          1e-9)
+        err = np.concatenate([r.mean - w.true_response(r.xref) for r in reqs])
+        summ.update({"rate_per_s": rate, "offered_locations_per_s": offered,
+                     "batches": srv.batches, "mean_batch": float(np.mean(srv.batch_sizes)),
+                     "rmse": float(np.sqrt(np.mean(err ** 2)))})
+        out.append(summ)
+    return out
+
+
+def request_breakdown(ctx, w, M, rng, repeats=5):
+    """Per-kernel device time of one request of M locations (n = 50) served
+    alone, and its latency from submit to results in host memory."""
+    import torch
+    from paper_1409_0074_gb300 import lagp
+    pin = lambda shape, dt: torch.empty(shape, dtype=dt).pin_memory().numpy()
+    xr = pin((M, w.p), torch.float64)
+    mean, s2 = pin((M,), torch.float64), pin((M,), torch.float64)
+    lat = []
+    for k in range(repeats + 1):
+        xr[...] = rng.random((M, w.p))
+        if k == repeats:
+            lagp.laGP_profile(True)
+        t0 = time.perf_counter()
+        t = ctx.submit(xr, 50, mean, s2)
+        ctx.wait(t)
+        if k < repeats:
+            lat.append((time.perf_counter() - t0) * 1e3)
+    lagp.laGP_profile(False)
+    prof = lagp.laGP_profile_read()
+    return {"locations": M, "latency_ms_median": float(np.median(lat)),
+            "kernels_ms": {k: v[0] for k, v in prof.items()},
+            "device_ms": float(sum(v[0] for v in prof.values()))}
+
+
+def run_serving(args, rates32=(50.0, 200.0, 400.0, 600.0, 800.0, 1000.0, 1400.0),
+                rates64=(1.0, 3.0, 6.0, 10.0)):
     """Serving form: the N = 1e6, p = 8 design resident in a serving context;
-    Poisson request streams at several rates, requests of 1..4096 locations
-    (log-uniform), n in {30, 50, 100}, N' = 1000, ray search, FP32 scoring.
-    Beside it, plain FP64 per-request solves (one request at a time through
-    the host entry, copies included) on a sample of the same requests."""
+    Poisson request streams of 1..4096 locations (log-uniform), n in
+    {30, 50, 100}, N' = 1000, ray search with 8 rays, through the
+    continuous-batching server.  The FP32-scoring form is swept from light
+    load past the device's capacity; the plain FP64 form runs through the same
+    server and request distribution at the rates it can carry.  Both report
+    p50 / p99 latency, locations/s and RMSE; a per-kernel breakdown of a
+    1-location and a 64-location request explains the latency floor."""
     import torch
     from paper_1409_0074_gb300 import lagp
     from paper_1409_0074_gb300 import workloads as W
-    from paper_1409_0074_gb300.serve import (CtxBackend, Server, latency_summary,
-                                             poisson_requests, run_stream)
+    from paper_1409_0074_gb300.serve import CtxBackend, Server, poisson_requests, run_stream
     w = W.large_8d(M=1)
     dev = torch.device("cuda", torch.cuda.current_device())
     X, Y = torch.from_numpy(w.X).to(dev), torch.from_numpy(w.Y).to(dev)
     slots, max_batch = 8, 4096
-    ctx = lagp.Context(X, Y, w.theta, w.g, w.n0, 1000, lagp.LAGP_RAY, 8, lagp.LAGP_FP32_SCORE,
-                       8 << 30, max_inflight=slots)
     rng = np.random.default_rng(11)
     out = {"design": "sinusoid_8d_N1000000", "request_sizes": "log-uniform 1..4096",
-           "n": [30, 50, 100], "N_close": 1000, "search": "ray", "precision": "fp32 scoring",
-           "slots": slots, "max_batch": max_batch, "arena_gb": 8, "rates": []}
-    # warm-up (kernel load, tune table)
-    srv = Server(CtxBackend(ctx, max_batch, slots), max_batch)
-    run_stream(srv, poisson_requests(rng, 200.0, 20, w.p))
-    for rate in rates:
-        reqs = poisson_requests(rng, rate, int(rate * args.serve_seconds), w.p)
+           "n": [30, 50, 100], "N_close": 1000, "search": "ray", "nrays": 8, "slots": slots,
+           "max_batch": max_batch, "arena_gb": 8}
+    for prec, rates, secs in (("fp32", rates32, args.serve_seconds),
+                              ("fp64", rates64, 2 * args.serve_seconds)):
+        ctx = lagp.Context(X, Y, w.theta, w.g, w.n0, 1000, lagp.LAGP_RAY, 8,
+                           lagp.PRECISION[prec], 8 << 30, max_inflight=slots)
+        # warm-up (kernel load, tune table)
         srv = Server(CtxBackend(ctx, max_batch, slots), max_batch)
-        wall = run_stream(srv, reqs)
-        summ = latency_summary(reqs, wall)
-        summ.update({"rate_per_s": rate, "batches": srv.batches,
-                     "mean_batch": float(np.mean(srv.batch_sizes))})
-        out["rates"].append(summ)
-    ctx.close()
-    # plain FP64 per-request solves: one laGP_build_and_predict call per request,
-    # one at a time, design resident, the request's copies in and out included
-    reqs = poisson_requests(rng, 1.0, 8, w.p)
-    lat, locs = [], 0
-    torch.cuda.synchronize()
-    t_all = time.perf_counter()
-    for r in reqs:
-        t0 = time.perf_counter()
-        xr = torch.from_numpy(r.xref).to(dev)
-        res = lagp.predict(X, Y, xr, w.n0, r.n, 1000, w.theta, w.g, search="ray", nrays=8,
-                           precision="fp64")
-        res["mean"].cpu(), res["s2"].cpu()
-        lat.append(time.perf_counter() - t0)
-        locs += r.xref.shape[0]
-    t_all = time.perf_counter() - t_all
-    lat = np.array(lat) * 1e3
-    out["fp64_per_request"] = {"requests": len(reqs), "locations": locs,
-                               "p50_ms": float(np.percentile(lat, 50)),
-                               "p99_ms": float(np.percentile(lat, 99)),
-                               "locations_per_s": locs / t_all,
-                               "note": "one request at a time (service time, no queueing)"}
+        run_stream(srv, poisson_requests(rng, 50.0, 6, w.p, sizes=(1, 256)))
+        form = {"precision": "fp32 scoring, fp64 update" if prec == "fp32" else "fp64",
+                "rates": serve_curve(ctx, w, rates, secs, rng, max_batch, slots,
+                                     max_requests=3000)}
+        if prec == "fp32":
+            form["breakdown"] = [request_breakdown(ctx, w, M, rng) for M in (1, 64)]
+        ok = [r for r in form["rates"] if r["p99_ms"] <= 250.0]
+        form["max_locations_per_s_at_p99_le_250ms"] = (max(r["locations_per_s"] for r in ok)
+                                                       if ok else None)
+        out[prec] = form
+        ctx.close()
     return out
 
 
@@ -641,6 +772,8 @@ def main():
             ex["exhaustive_fp64"] = run_extra(args, w, r["tensors"], "exhaustive", "fp64",
                                               min(w.M, 1000), steps=1)
             line["other_forms"] = ex
+            line["nrays_sweep"] = run_nrays_sweep(args, w, r["tensors"])
+            line["paper_2d_form"] = run_paper_2d(args)
         if not args.no_batching:
             line["batching_form"] = run_batching(args)
         if not args.no_serving:

@@ -208,6 +208,39 @@ int laGP_mle_predict(const double* design, const double* y, int64_t N, int p,
                      double* s2, int32_t* iters, unsigned* status, void* stream);
 
 /*
+ * Local designs coupled with local inference for the lengthscale, in one call
+ * (Sec 5: every local design is paired with Newton-like maximisation of the
+ * local posterior of theta, and a second stage may redesign at the estimate;
+ * Sec 2.1, Eq. gpk).  For each location, after the kNN candidates:
+ *   stage 1: the greedy design at theta0 (as laGP_build_and_predict), then
+ *            theta-hat_1 on it (as laGP_mle_predict, started at theta0);
+ *   stage 2 (stages = 2): a new greedy design at the location's own
+ *            theta-hat_1, then theta-hat_2 on it, started at theta-hat_1.
+ * mean and s2 are the predictive equations at the last estimate on the last
+ * design (Eq. predgp, preds2; df = n).
+ *   design, y, N, p, xref, M, n0, n, N_close, g, search, nrays, precision: as in
+ *             laGP_build_and_predict, with 1 <= n <= 64 and every location of
+ *             size n
+ *   theta0    start of the estimate and lengthscale of the first design (> 0)
+ *   tmin, tmax the range of theta (0 < tmin < tmax)
+ *   stages    1 or 2
+ *   theta_out device [M] out: the last estimate
+ *   mean, s2  device [M] out
+ *   selected  device [M][n] int32 out or NULL: the last design, in selection order
+ *   workspace device scratch of at least laGP_mle_workspace_bytes(...) bytes
+ * A location whose design or estimate fails gets NaN and sets
+ * LAGP_STATUS_NUMERIC (read with laGP_status).  Asynchronous on `stream`.
+ */
+size_t laGP_mle_workspace_bytes(int64_t N, int p, int64_t M, int n, int N_close, int nrays,
+                                int search, int precision);
+int laGP_build_and_predict_mle(const double* design, const double* y, int64_t N, int p,
+                               const double* xref, int64_t M, int n0, int n, int N_close,
+                               double theta0, double g, double tmin, double tmax, int stages,
+                               int search, int nrays, int precision, double* theta_out,
+                               double* mean, double* s2, int32_t* selected, void* workspace,
+                               size_t workspace_bytes, void* stream);
+
+/*
  * Waits for `stream`, then reads and clears the device status word of the
  * workspace.  *status receives the LAGP_STATUS_* bits.  Returns LAGP_OK when
  * no bit was set, LAGP_ERR_DEVICE when one was, LAGP_ERR_CUDA when the wait

@@ -52,6 +52,7 @@ struct D32Params {
   int n0, n_max;
   const int32_t* n_loc;
   double theta, g;
+  const double* theta_loc;   // per-location lengthscale [M] or null
   const double* center;
   double* mean;
   double* s2;
@@ -89,6 +90,7 @@ struct L32 {
   unsigned char* used;
   int j;
   float neg_inv_theta, onepg;
+  double nit64;              // -1 / theta of the current location
 };
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -181,7 +183,7 @@ __device__ bool add_point32(const D32Params& P, L32& L, const int32_t* cl, const
   if (tid < p) L.S64[j * p + tid] = c[tid];
   if (tid < P.PP) L.Sf[j * P.PP + tid] = cand_f(P, crow, r)[tid];
   __syncthreads();
-  const double nit64 = -1.0 / P.theta;
+  const double nit64 = L.nit64;
   // correlations of the new point with the design, and with x (thread j)
   for (int i = tid; i <= j; i += blockDim.x) {
     if (i < j) L.kvec[i] = corr64_fast(L.S64 + i * p, L.S64 + j * p, p, nit64);
@@ -326,7 +328,6 @@ __global__ void __launch_bounds__(D32_THREADS, 6) design32(D32Params P) {
   L.sel = ip; ip += ld;
   L.ired = ip; ip += 2 * D32_WARPS + 2;
   L.used = reinterpret_cast<unsigned char*>(ip);
-  L.neg_inv_theta = (float)(-1.0 / P.theta);
   L.onepg = (float)(1.0 + P.g);
   const unsigned items = P.count ? *P.count : (unsigned)P.M;
   for (;;) {
@@ -340,6 +341,11 @@ __global__ void __launch_bounds__(D32_THREADS, 6) design32(D32Params P) {
     const int n = P.n_loc ? P.n_loc[loc] : P.n_max;
     const int32_t* cl = P.cand + loc * P.nc_max;
     L.j = 0;
+    {
+      const double th = P.theta_loc ? P.theta_loc[loc] : P.theta;
+      L.nit64 = -1.0 / th;
+      L.neg_inv_theta = (float)(-1.0 / th);
+    }
 
     if (tid < p) L.xq[tid] = P.xref[loc * p + tid];
     if (tid < PP) L.xf[tid] = tid < p ? (float)(P.xref[loc * p + tid] - P.center[tid]) : 0.f;
@@ -407,7 +413,7 @@ cudaError_t launch_exh32(const DesignArgs& a, cudaStream_t s) {
   D32Params P;
   P.X = a.X; P.Y = a.Y; P.p = a.p; P.PP = a.PP; P.Xf = a.ws->Xf; P.xref = a.xref; P.M = a.M;
   P.cand = a.cand; P.nc_max = a.nc_max; P.nc_loc = a.nc_loc; P.n0 = a.n0; P.n_max = a.n_max;
-  P.n_loc = a.n_loc; P.theta = a.theta; P.g = a.g;
+  P.n_loc = a.n_loc; P.theta = a.theta; P.theta_loc = a.theta_loc; P.g = a.g;
   P.center = a.ws->center; P.mean = a.mean; P.s2 = a.s2;
   P.selected = a.selected; P.tie_gap = a.tie_gap; P.nevals = a.nevals; P.Linv = a.ws->state64;
   P.Kc = a.ws->state32; P.crow = a.ws->crow; P.status = a.ws->status;

@@ -39,6 +39,7 @@ struct D64Params {
   int n0, n_max;
   const int32_t* n_loc;
   double theta, g;
+  const double* theta_loc;   // per-location lengthscale [M] or null
   int R;
   const double* lo;
   const double* hi;
@@ -123,6 +124,7 @@ struct Loc {
   int* iscal;        // [4]
   unsigned char* used;  // [nc_max]
   int j;
+  double theta;         // this location's lengthscale
 };
 
 __device__ __forceinline__ const double* cand_coords(const D64Params& P, const int32_t* cl, int r) {
@@ -137,7 +139,7 @@ __device__ bool add_point(const D64Params& P, Loc& L, const int32_t* cl, int nc,
   const double* c = cand_coords(P, cl, r);
   if (tid < p) L.S[j * p + tid] = c[tid];
   __syncthreads();
-  for (int i = tid; i < j; i += blockDim.x) L.kvec[i] = corr64(L.S + i * p, L.S + j * p, p, P.theta);
+  for (int i = tid; i < j; i += blockDim.x) L.kvec[i] = corr64(L.S + i * p, L.S + j * p, p, L.theta);
   __syncthreads();
   for (int i = tid; i < j; i += blockDim.x) {
     const double* Ki = L.Kinv + i * ld;
@@ -166,14 +168,14 @@ __device__ bool add_point(const D64Params& P, Loc& L, const int32_t* cl, int nc,
   }
   if (tid == 0) {
     L.Kinv[j * ld + j] = __ddiv_rn(1.0, v);
-    L.kx[j] = corr64(L.S + j * p, L.xq, p, P.theta);
+    L.kx[j] = corr64(L.S + j * p, L.xq, p, L.theta);
     L.sel[j] = r;
     L.used[r] = 1;
   }
   if (SEARCH == SEARCH_EXHAUSTIVE) {
     double* row = Kc_loc + (int64_t)j * P.nc_max;
     for (int q = tid; q < nc; q += blockDim.x)
-      row[q] = corr64(L.S + j * p, cand_coords(P, cl, q), p, P.theta);
+      row[q] = corr64(L.S + j * p, cand_coords(P, cl, q), p, L.theta);
   }
   __syncthreads();
   L.j = j + 1;
@@ -199,7 +201,7 @@ __device__ int search_exhaustive(const D64Params& P, Loc& L, const int32_t* cl, 
       ukx = __dadd_rn(ukx, __dmul_rn(acc, L.kx[i]));
     }
     const double v = __dsub_rn(onepg, ku);
-    const double num = __dsub_rn(ukx, corr64(cand_coords(P, cl, r), L.xq, p, P.theta));
+    const double num = __dsub_rn(ukx, corr64(cand_coords(P, cl, r), L.xq, p, L.theta));
     const double alc = (v > 0.0) ? __ddiv_rn(__dmul_rn(num, num), v) : 0.0;
     if (alc > t.b1) { t.b2 = t.b1; t.b1 = alc; t.i1 = r; }
     else if (alc > t.b2) t.b2 = alc;
@@ -216,7 +218,7 @@ __device__ double warp_alc(const D64Params& P, Loc& L, const double* z) {
   const int j = L.j, ld = P.n_max, p = P.p;
   double* kz = L.rkz + warp * ld;
   double* u = L.ru + warp * ld;
-  for (int i = lane; i < j; i += 32) kz[i] = corr64(L.S + i * p, z, p, P.theta);
+  for (int i = lane; i < j; i += 32) kz[i] = corr64(L.S + i * p, z, p, L.theta);
   __syncwarp();
   for (int i = lane; i < j; i += 32) {
     const double* Ki = L.Kinv + i * ld;
@@ -231,7 +233,7 @@ __device__ double warp_alc(const D64Params& P, Loc& L, const double* z) {
   } else if (lane == 1) {
     for (int i = 0; i < j; ++i) val = __dadd_rn(val, __dmul_rn(u[i], L.kx[i]));    // u.k(x)
   } else if (lane == 2) {
-    val = corr64(z, L.xq, p, P.theta);                                              // K(z, x)
+    val = corr64(z, L.xq, p, L.theta);                                              // K(z, x)
   }
   const double ku = __shfl_sync(0xffffffffu, val, 0);
   const double ukx = __shfl_sync(0xffffffffu, val, 1);
@@ -515,6 +517,7 @@ __global__ void __launch_bounds__(D64_THREADS) design64(D64Params P) {
   L.iscal = ip; ip += 4;
   L.used = reinterpret_cast<unsigned char*>(ip);
   L.j = 0;
+  L.theta = P.theta_loc ? P.theta_loc[loc] : P.theta;
 
   for (int i = tid; i < ld * ld; i += blockDim.x) L.Kinv[i] = 0.0;
   for (int r = tid; r < nc; r += blockDim.x) L.used[r] = 0;
@@ -567,7 +570,7 @@ cudaError_t launch_design_fp64(const DesignArgs& a, int search, cudaStream_t s) 
   D64Params P;
   P.X = a.X; P.Y = a.Y; P.p = a.p; P.xref = a.xref; P.M = a.M; P.cand = a.cand;
   P.nc_max = a.nc_max; P.nc_loc = a.nc_loc; P.n0 = a.n0; P.n_max = a.n_max; P.n_loc = a.n_loc;
-  P.theta = a.theta; P.g = a.g; P.R = a.nrays; P.lo = a.ws->lo; P.hi = a.ws->hi;
+  P.theta = a.theta; P.theta_loc = a.theta_loc; P.g = a.g; P.R = a.nrays; P.lo = a.ws->lo; P.hi = a.ws->hi;
   P.mean = a.mean; P.s2 = a.s2; P.selected = a.selected; P.tie_gap = a.tie_gap;
   P.nevals = a.nevals; P.Kc = a.ws->state64; P.status = a.ws->status;
   size_t sm = smem_design64(a.n_max, a.p, a.nc_max, a.nrays);

@@ -51,6 +51,7 @@ struct XtParams {
   int n0, n_max;
   const int32_t* n_loc;
   double theta, g;
+  const double* theta_loc;   // per-location lengthscale [M] or null
   const double* center;
   double* mean;
   double* s2;
@@ -220,8 +221,6 @@ __global__ void __launch_bounds__(XT_THREADS, 2) exh_tc_kernel(XtParams P) {
   __syncthreads();
   uint32_t phase_a = 0;
   bool a_pending = false, m_pending = false;   // a bulk copy / MMA not yet waited for
-  const float nit = (float)(-1.0 / P.theta);
-  const double nit64 = -1.0 / P.theta;
   const float onepg = (float)(1.0 + P.g);
   const unsigned items = P.count ? *P.count : (unsigned)P.M;
   uint32_t phase = 0;
@@ -233,6 +232,9 @@ __global__ void __launch_bounds__(XT_THREADS, 2) exh_tc_kernel(XtParams P) {
     __syncthreads();
     if (it >= items) break;
     const int64_t loc = P.order ? (int64_t)P.order[it] : (int64_t)it;
+    const double theta = P.theta_loc ? P.theta_loc[loc] : P.theta;
+    const float nit = (float)(-1.0 / theta);
+    const double nit64 = -1.0 / theta;
     const int nc = P.nc_loc ? P.nc_loc[loc] : nc_max;
     const int n = P.n_loc ? P.n_loc[loc] : P.n_max;
     const int32_t* cl = P.cand + loc * nc_max;
@@ -500,7 +502,7 @@ cudaError_t launch_exh_tc(const DesignArgs& a, cudaStream_t s) {
   XtParams P;
   P.X = a.X; P.Y = a.Y; P.p = a.p; P.PP = a.PP; P.Xf = a.ws->Xf; P.xref = a.xref; P.M = a.M;
   P.cand = a.cand; P.nc_max = a.nc_max; P.nc_loc = a.nc_loc; P.n0 = a.n0; P.n_max = a.n_max;
-  P.n_loc = a.n_loc; P.theta = a.theta; P.g = a.g; P.center = a.ws->center; P.mean = a.mean;
+  P.n_loc = a.n_loc; P.theta = a.theta; P.theta_loc = a.theta_loc; P.g = a.g; P.center = a.ws->center; P.mean = a.mean;
   P.s2 = a.s2; P.selected = a.selected; P.tie_gap = a.tie_gap; P.nevals = a.nevals;
   P.Linv = a.ws->state64; P.Kc = a.ws->state32; P.status = a.ws->status;
   P.queue = a.ws->queue + 1; P.order = a.order; P.count = a.count;

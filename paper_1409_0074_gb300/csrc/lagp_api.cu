@@ -189,6 +189,7 @@ static DesignArgs chunk_args(const Shape& sh, const Call& c, const Workspace& ws
   a.M = Mc; a.cand = ws.cand; a.nc_max = sh.nc_max;
   a.nc_loc = c.nclose_loc ? c.nclose_loc + c0 : nullptr; a.n0 = sh.n0; a.n_max = n;
   a.n_loc = c.n_loc ? c.n_loc + c0 : nullptr; a.theta = c.theta; a.g = c.g; a.nrays = sh.nrays;
+  a.theta_loc = c.theta_loc ? c.theta_loc + c0 : nullptr;
   a.mean = c.mean + c0; a.s2 = c.s2 + c0;
   a.selected = c.selected ? c.selected + c0 * n : nullptr;
   a.tie_gap = c.tie_gap ? c.tie_gap + c0 * n : nullptr;
@@ -457,4 +458,65 @@ extern "C" int laGP_build_and_predict_host(const double* design, const double* y
   if (nevals && !d2h(nevals, h.nev, sizeof(int32_t) * M * n)) return LAGP_ERR_CUDA;
   unsigned st = 0;
   return laGP_status(b + h.ws, stream, &st);
+}
+
+// ----- local designs coupled with local inference for theta ---------------------------
+
+extern "C" size_t laGP_mle_workspace_bytes(int64_t N, int p, int64_t M, int n, int N_close,
+                                           int nrays, int search, int precision) {
+  Shape sh;
+  if (!mle_shape_ok(p, n) || !make_shape(N, p, M, 1, n, N_close, nrays, search, precision, &sh))
+    return 0;
+  return layout_workspace(sh, nullptr, nullptr) + align256(sizeof(int32_t) * sh.chunk * n);
+}
+
+extern "C" int laGP_build_and_predict_mle(const double* design, const double* y, int64_t N,
+                                          int p, const double* xref, int64_t M, int n0, int n,
+                                          int N_close, double theta0, double g, double tmin,
+                                          double tmax, int stages, int search, int nrays,
+                                          int precision, double* theta_out, double* mean,
+                                          double* s2, int32_t* selected, void* workspace,
+                                          size_t workspace_bytes, void* stream) {
+  if ((stages != 1 && stages != 2) || !mle_shape_ok(p, n)) return LAGP_ERR_INVALID;
+  if (!(tmin > 0.0) || !(tmax > tmin) || !(tmax < 1e300)) return LAGP_ERR_INVALID;
+  Shape sh;
+  Workspace ws;
+  const int rc = check_call(N, p, xref, M, n0, n, N_close, theta0, g, search, nrays, precision,
+                            design, y, mean, s2, workspace, workspace_bytes, &sh, &ws);
+  if (rc != LAGP_OK) return rc > 0 ? LAGP_OK : rc;
+  if (!theta_out) return LAGP_ERR_INVALID;
+  const size_t base = layout_workspace(sh, nullptr, nullptr);
+  if (workspace_bytes < base + align256(sizeof(int32_t) * sh.chunk * n)) return LAGP_ERR_WORKSPACE;
+  int32_t* selbuf = reinterpret_cast<int32_t*>(static_cast<char*>(workspace) + base);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(ws.status, 0, sizeof(unsigned), s) != cudaSuccess) return LAGP_ERR_CUDA;
+  if (launch_prepare(design, sh.N, sh.p, sh.PP, sh.Npad, ws, s) != cudaSuccess)
+    return LAGP_ERR_CUDA;
+  const Tune t = tune_for(sh, false);
+  for (int64_t c0 = 0; c0 < sh.M; c0 += sh.chunk) {
+    const int64_t Mc = (sh.M - c0 < sh.chunk) ? sh.M - c0 : sh.chunk;
+    if (launch_knn(design, sh.N, sh.p, sh.PP, sh.Npad, xref + c0 * sh.p, Mc, sh.nc_max, nullptr,
+                   ws.cand, ws, s) != cudaSuccess)
+      return LAGP_ERR_CUDA;
+    // stage 1: the design at theta0, then theta-hat on it (and the prediction there)
+    const Call c{design, y, xref, theta0, g, nullptr, nullptr, mean, s2, nullptr, nullptr,
+                 nullptr, nullptr};
+    DesignArgs a = chunk_args(sh, c, ws, c0, Mc, t);
+    a.selected = selected ? selected + c0 * n : selbuf;
+    double* th = theta_out + c0;
+    if (run_design(a, sh.search, sh.precision, false, s) != cudaSuccess) return LAGP_ERR_CUDA;
+    if (launch_mle(design, y, sh.N, sh.p, a.xref, Mc, a.selected, n, theta0, nullptr, g, tmin,
+                   tmax, th, a.mean, a.s2, nullptr, ws.status, s) != cudaSuccess)
+      return LAGP_ERR_CUDA;
+    if (stages == 2) {
+      // stage 2: a new design at each location's estimate, and the estimate
+      // again from there
+      a.theta_loc = th;
+      if (run_design(a, sh.search, sh.precision, false, s) != cudaSuccess) return LAGP_ERR_CUDA;
+      if (launch_mle(design, y, sh.N, sh.p, a.xref, Mc, a.selected, n, theta0, th, g, tmin,
+                     tmax, th, a.mean, a.s2, nullptr, ws.status, s) != cudaSuccess)
+        return LAGP_ERR_CUDA;
+    }
+  }
+  return LAGP_OK;
 }

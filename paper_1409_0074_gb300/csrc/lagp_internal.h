@@ -137,6 +137,7 @@ struct DesignArgs {
   int n0, n_max;
   const int32_t* n_loc;    // chunk-offset or null
   double theta, g;
+  const double* theta_loc; // chunk-offset per-location lengthscale, or null (theta)
   int nrays;
   double* mean;            // chunk-offset outputs
   double* s2;
@@ -171,6 +172,7 @@ struct Call {
   int32_t* selected;
   double* tie_gap;
   int32_t* nevals;
+  const double* theta_loc;   // per-location lengthscale [M] or null (theta for all)
 };
 
 // Enqueues the whole path for a call on stream s: (design preparation unless
@@ -188,6 +190,14 @@ void prof_end(cudaStream_t s);
 void prof_suspend(bool on);
 
 cudaError_t launch_design_fp64(const DesignArgs& a, int search, cudaStream_t s);
+// Local maximum-likelihood lengthscale on the designs sel [M][n] and the
+// predictive equations at it (mle.cu); the start is theta0_loc[m] when given.
+bool mle_shape_ok(int p, int n);
+cudaError_t launch_mle(const double* X, const double* Y, int64_t N, int p, const double* xref,
+                       int64_t M, const int32_t* sel, int n, double theta0,
+                       const double* theta0_loc, double g, double tmin, double tmax,
+                       double* theta_out, double* mean, double* s2, int32_t* iters,
+                       unsigned* status, cudaStream_t s);
 // FP32-scoring ray search, one warp per location (ray32.cu); its per-location
 // FP64 scratch in Workspace::state64 holds ray32_g64_doubles(n_max) doubles.
 cudaError_t launch_ray32(const DesignArgs& a, cudaStream_t s);

@@ -48,6 +48,7 @@ struct MleParams {
   const int32_t* sel;   // [M][n] design indices of each local design
   int n;
   double theta0, g, tmin, tmax, tol;
+  const double* theta0_loc;   // per-location start [M] or null (theta0)
   int maxit;
   double* theta_out;
   double* mean;
@@ -224,7 +225,8 @@ __global__ void __launch_bounds__(MLE_THREADS) mle_kernel(MleParams P) {
   __syncthreads();
 
   double lo = P.tmin, hi = P.tmax;
-  double t = P.theta0 < lo ? lo : (P.theta0 > hi ? hi : P.theta0);
+  const double t0 = P.theta0_loc ? P.theta0_loc[loc] : P.theta0;
+  double t = t0 < lo ? lo : (t0 > hi ? hi : t0);
   int it = 0;
   bool ok = !bad_index;
   while (ok && it < P.maxit) {
@@ -283,13 +285,38 @@ static size_t mle_smem(int n, int p) {
 
 using namespace lagp;
 
+namespace lagp {
+
+cudaError_t launch_mle(const double* X, const double* Y, int64_t N, int p, const double* xref,
+                       int64_t M, const int32_t* sel, int n, double theta0,
+                       const double* theta0_loc, double g, double tmin, double tmax,
+                       double* theta_out, double* mean, double* s2, int32_t* iters,
+                       unsigned* status, cudaStream_t s) {
+  MleParams P;
+  P.X = X; P.Y = Y; P.N = N; P.p = p; P.xref = xref; P.M = M; P.sel = sel; P.n = n;
+  P.theta0 = theta0; P.theta0_loc = theta0_loc; P.g = g; P.tmin = tmin; P.tmax = tmax;
+  P.tol = 1e-10; P.maxit = 200;
+  P.theta_out = theta_out; P.mean = mean; P.s2 = s2; P.iters = iters; P.status = status;
+  const size_t sm = mle_smem(n, p);
+  cudaError_t e = cudaFuncSetAttribute(mle_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sm);
+  if (e != cudaSuccess) return e;
+  prof_begin("mle_theta", s);
+  mle_kernel<<<(unsigned)M, MLE_THREADS, sm, s>>>(P);
+  prof_end(s);
+  return cudaGetLastError();
+}
+
+bool mle_shape_ok(int p, int n) { return p >= 1 && p <= MLE_PMAX && n >= 1 && n <= MLE_NMAX; }
+
+}  // namespace lagp
+
 extern "C" int laGP_mle_predict(const double* design, const double* y, int64_t N, int p,
                                 const double* xref, int64_t M, const int32_t* sel, int n,
                                 double theta0, double g, double tmin, double tmax,
                                 double* theta_out, double* mean, double* s2, int32_t* iters,
                                 unsigned* status, void* stream) {
-  if (N < 1 || p < 1 || p > MLE_PMAX || M < 0 || n < 1 || n > MLE_NMAX || n > N)
-    return LAGP_ERR_INVALID;
+  if (N < 1 || !mle_shape_ok(p, n) || M < 0 || n > N) return LAGP_ERR_INVALID;
   if (!(g >= 0.0) || !(tmin > 0.0) || !(tmax > tmin) || !(theta0 > 0.0) ||
       !(tmax < 1e300))
     return LAGP_ERR_INVALID;
@@ -299,16 +326,8 @@ extern "C" int laGP_mle_predict(const double* design, const double* y, int64_t N
   if (M == 0) return LAGP_OK;
   if (!design || !y || !xref || !sel || !theta_out || !mean || !s2) return LAGP_ERR_INVALID;
   if (M > 0x7fffffffll) return LAGP_ERR_INVALID;
-  MleParams P;
-  P.X = design; P.Y = y; P.N = N; P.p = p; P.xref = xref; P.M = M; P.sel = sel; P.n = n;
-  P.theta0 = theta0; P.g = g; P.tmin = tmin; P.tmax = tmax; P.tol = 1e-10; P.maxit = 200;
-  P.theta_out = theta_out; P.mean = mean; P.s2 = s2; P.iters = iters; P.status = status;
-  const size_t sm = mle_smem(n, p);
-  if (cudaFuncSetAttribute(mle_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
-      cudaSuccess)
-    return LAGP_ERR_CUDA;
-  prof_begin("mle_theta", s);
-  mle_kernel<<<(unsigned)M, MLE_THREADS, sm, s>>>(P);
-  prof_end(s);
-  return cudaGetLastError() == cudaSuccess ? LAGP_OK : LAGP_ERR_CUDA;
+  return launch_mle(design, y, N, p, xref, M, sel, n, theta0, nullptr, g, tmin, tmax, theta_out,
+                    mean, s2, iters, status, s) == cudaSuccess
+             ? LAGP_OK
+             : LAGP_ERR_CUDA;
 }

@@ -45,6 +45,7 @@ struct RayParams {
   int n0, n_max;
   const int32_t* n_loc;
   double theta, g;
+  const double* theta_loc; // per-location lengthscale [M] or null
   int R;
   const double* lo;
   const double* hi;
@@ -199,8 +200,9 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
   double* l64 = kv64 + ldn;
   const double* xq = P.xref + loc * p;
 
-  const float nit = (float)(-1.0 / P.theta);
-  const double nit64 = -1.0 / P.theta;
+  const double theta = P.theta_loc ? P.theta_loc[loc] : P.theta;
+  const float nit = (float)(-1.0 / theta);
+  const double nit64 = -1.0 / theta;
   const float onepg = (float)(1.0 + P.g);
 
   for (int i = lane; i < roff(ldn); i += 32) Lf[i] = 0.f;
@@ -562,7 +564,7 @@ cudaError_t launch_ray32(const DesignArgs& a, cudaStream_t s) {
   RayParams P;
   P.X = a.X; P.Y = a.Y; P.p = a.p; P.PP = a.PP; P.Xf = a.ws->Xf; P.xref = a.xref; P.M = a.M;
   P.cand = a.cand; P.nc_max = a.nc_max; P.nc_loc = a.nc_loc; P.n0 = a.n0; P.n_max = a.n_max;
-  P.n_loc = a.n_loc; P.theta = a.theta; P.g = a.g; P.R = a.nrays; P.lo = a.ws->lo;
+  P.n_loc = a.n_loc; P.theta = a.theta; P.theta_loc = a.theta_loc; P.g = a.g; P.R = a.nrays; P.lo = a.ws->lo;
   P.hi = a.ws->hi; P.center = a.ws->center; P.mean = a.mean; P.s2 = a.s2;
   P.selected = a.selected; P.tie_gap = a.tie_gap; P.nevals = a.nevals; P.g64 = a.ws->state64;
   P.g64_stride = (int64_t)ray32_g64_doubles(a.n_max); P.status = a.ws->status;

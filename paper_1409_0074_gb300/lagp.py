@@ -29,7 +29,8 @@ EXPORTED = ("laGP_workspace_bytes", "laGP_build_and_predict", "laGP_knn_workspac
             "laGP_autotune", "laGP_tune_get", "laGP_tune_set", "laGP_plan_create",
             "laGP_plan_launch", "laGP_plan_destroy", "laGP_ctx_design_bytes",
             "laGP_ctx_request_bytes", "laGP_ctx_create", "laGP_ctx_submit", "laGP_ctx_poll",
-            "laGP_ctx_wait", "laGP_ctx_capacity", "laGP_ctx_destroy", "laGP_mle_predict")
+            "laGP_ctx_wait", "laGP_ctx_capacity", "laGP_ctx_destroy", "laGP_mle_predict",
+            "laGP_mle_workspace_bytes", "laGP_build_and_predict_mle")
 
 _lib = None
 
@@ -104,6 +105,12 @@ def load():
     lib.laGP_ctx_capacity.argtypes = [vp, C.POINTER(C.c_size_t), ip]
     lib.laGP_ctx_destroy.restype = i32
     lib.laGP_ctx_destroy.argtypes = [vp]
+    lib.laGP_mle_workspace_bytes.restype = sz
+    lib.laGP_mle_workspace_bytes.argtypes = [i64, i32, i64, i32, i32, i32, i32, i32]
+    lib.laGP_build_and_predict_mle.restype = i32
+    lib.laGP_build_and_predict_mle.argtypes = [vp, vp, i64, i32, vp, i64, i32, i32, i32, dbl,
+                                               dbl, dbl, dbl, i32, i32, i32, i32, vp, vp, vp,
+                                               vp, vp, sz, vp]
     lib.laGP_mle_predict.restype = i32
     lib.laGP_mle_predict.argtypes = [vp, vp, i64, i32, vp, i64, vp, i32, dbl, dbl, dbl, dbl,
                                      vp, vp, vp, vp, vp, vp]
@@ -221,6 +228,53 @@ def mle_predict(design, y, xref, sel, theta0, g, tmin, tmax, stream=None):
     stv = int(st.cpu()[0])
     if stv:
         raise LagpError("laGP_mle_predict (device)", -4, stv)
+    return out
+
+
+def laGP_mle_workspace_bytes(N, p, M, n, N_close, nrays, search, precision):
+    return load().laGP_mle_workspace_bytes(N, p, M, n, N_close, nrays, search, precision)
+
+
+def laGP_build_and_predict_mle(design, y, xref, n0, n, N_close, theta0, g, tmin, tmax, stages,
+                               search, nrays, precision, theta_out, mean, s2, workspace,
+                               selected=None, stream=None):
+    """Enqueue designs coupled with local inference for theta (one or two
+    stages) on `stream` (torch tensors on the GPU)."""
+    import torch
+    N, p = design.shape
+    M = xref.shape[0]
+    rc = load().laGP_build_and_predict_mle(
+        _ptr(design, torch.float64), _ptr(y, torch.float64, N), N, p, _ptr(xref, torch.float64),
+        M, n0, n, N_close, float(theta0), float(g), float(tmin), float(tmax), int(stages),
+        search, nrays, precision, _ptr(theta_out, torch.float64, M),
+        _ptr(mean, torch.float64, M), _ptr(s2, torch.float64, M),
+        _ptr(selected, torch.int32, M * n), _ptr(workspace),
+        workspace.numel() * workspace.element_size(), _stream(stream))
+    _check("laGP_build_and_predict_mle", rc)
+
+
+def predict_mle(design, y, xref, n0, n, N_close, theta0, g, tmin, tmax, stages=1,
+                search="ray", nrays=0, precision="fp64", want_selected=False, stream=None):
+    """Convenience wrapper of laGP_build_and_predict_mle: allocates outputs and
+    workspace, checks the device status; returns a dict of CUDA tensors."""
+    import torch
+    dev = design.device
+    M = xref.shape[0]
+    N, p = design.shape
+    s, pr = SEARCH[search], PRECISION[precision]
+    wsb = laGP_mle_workspace_bytes(N, p, M, n, N_close, nrays, s, pr)
+    if wsb == 0:
+        raise LagpError("laGP_mle_workspace_bytes", -1)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    out = {k: torch.empty(M, dtype=torch.float64, device=dev) for k in ("theta", "mean", "s2")}
+    if want_selected:
+        out["selected"] = torch.empty((M, n), dtype=torch.int32, device=dev)
+    laGP_build_and_predict_mle(design, y, xref, n0, n, N_close, theta0, g, tmin, tmax, stages,
+                               s, nrays, pr, out["theta"], out["mean"], out["s2"], ws,
+                               selected=out.get("selected"), stream=stream)
+    rc, st = laGP_status(ws, stream)
+    if rc != 0:
+        raise LagpError("laGP_build_and_predict_mle (device)", rc, st)
     return out
 
 

@@ -57,11 +57,12 @@ def check_fp32_form(w, g, o, rmse_tol, max_gap, first_step_gap=None):
     if same.any():
         rel = np.abs(g["s2"][same] - o["s2"][same]) / o["s2"][same]
         assert np.all(rel <= 1e-4), rel.max()
-    # out-of-sample accuracy: the RMSE ratio over the sampled locations is a
-    # noisy estimate of the ratio over the workload (a few locations whose
-    # designs differ dominate it), so the bar is on its lower 3-sigma bound
+    # out-of-sample accuracy: the RMSE ratio over the sampled locations (the
+    # point estimate; callers size the sample so that it is a few tenths of a
+    # percent from the ratio over the whole workload)
     r, se = rmse_ratio(g["mean"], o["mean"], w.Ytrue)
-    assert r - 3 * se <= 1 + rmse_tol, (r, se)
+    if rmse_tol is not None:
+        assert r <= 1 + rmse_tol, (r, se)
     # a design first departs from the oracle's only where the oracle's own
     # decision was close (FP32 scores resolve relative gaps of about 1e-4)
     gaps, first = [], []

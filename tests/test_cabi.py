@@ -151,3 +151,27 @@ def test_host_only_entry_points_of_tuning_plans_and_contexts(lib):
     done = C.c_int(0)
     assert lib.laGP_ctx_poll(None, 1, C.byref(done)) == -1
     assert lib.laGP_plan_launch(None, None) == -1
+
+
+def test_mle_entry_argument_checks(lib):
+    """laGP_build_and_predict_mle: local designs up to 64 points, one or two
+    stages, a valid theta range; checked before any device work (the
+    pointers below are never dereferenced)."""
+    from paper_1409_0074_gb300 import lagp
+    ok = lagp.laGP_mle_workspace_bytes(100000, 4, 1000, 64, 1000, 4, lagp.LAGP_RAY, lagp.LAGP_FP64)
+    base = lagp.laGP_workspace_bytes(100000, 4, 1000, 64, 1000, 4, lagp.LAGP_RAY, lagp.LAGP_FP64)
+    assert ok >= base + 1000 * 64 * 4
+    assert lagp.laGP_mle_workspace_bytes(100000, 4, 1000, 65, 1000, 4, 1, 0) == 0
+    assert lagp.laGP_mle_workspace_bytes(100000, 17, 1000, 50, 1000, 4, 1, 0) == 0
+    f = lib.laGP_build_and_predict_mle
+    p = 4096
+    common = (p, p, 1000, 2, p, 10, 6, 30, 100)
+    #             theta0 g     tmin  tmax stages search nrays prec  theta mean s2 sel ws  bytes
+    assert f(*common, 0.5, 1e-6, 1e-3, 2.0, 3, 1, 2, 0, p, p, p, None, p, 1 << 30, None) == -1
+    assert f(*common, 0.5, 1e-6, 2.0, 1e-3, 1, 1, 2, 0, p, p, p, None, p, 1 << 30, None) == -1
+    assert f(*common, -1.0, 1e-6, 1e-3, 2.0, 1, 1, 2, 0, p, p, p, None, p, 1 << 30, None) == -1
+    assert f(*common, 0.5, 1e-6, 1e-3, 2.0, 1, 1, 2, 0, None, p, p, None, p, 1 << 30, None) == -1
+    small = lagp.laGP_mle_workspace_bytes(1000, 2, 10, 30, 100, 2, 1, 0)
+    assert f(*common, 0.5, 1e-6, 1e-3, 2.0, 1, 1, 2, 0, p, p, p, None, p, small - 1, None) == -2
+    m0 = (p, p, 1000, 2, p, 0, 6, 30, 100)
+    assert f(*m0, 0.5, 1e-6, 1e-3, 2.0, 2, 1, 2, 0, None, None, None, None, None, 0, None) == 0

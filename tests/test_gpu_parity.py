@@ -6,7 +6,10 @@ that location is excused; mean and s2 of the other locations within 1e-10
 relative.  (The kernels follow the oracle's operation order, so in practice
 every location is bit-identical; the tests report that count.)
 FP32-scoring form: s2 within 1e-4 relative at locations whose design equals
-the oracle's, and out-of-sample RMSE within 1% of the oracle's.
+the oracle's, and out-of-sample RMSE within 1% of the oracle's (the point
+estimate over the sampled locations).  On the 4-d workload, whose K_n reach
+condition numbers of ~1e7, the FP32 form misses that bar; those tests are
+marked as expected failures with the measured ratios.
 kNN: candidate lists bit-exact (indices are integers).
 """
 import numpy as np
@@ -276,28 +279,31 @@ def test_fp64_paper_scale_4d_sample(lagp, paper4d, search):
     assert ident >= 0.9 * w.M
 
 
+@pytest.mark.xfail(reason="FP32 scoring at cond(K) ~1e7: over all 10,000 locations of the 4-d "
+                   "workload the FP32-form ray RMSE measured 1.3% above the FP64 form's",
+                   strict=False)
 def test_fp32_score_ray_paper_scale_4d_sample(lagp, paper4d):
-    """4-d workload (theta = 0.25, cond K_50 up to ~1e7): over all 10,000
-    locations the FP32-form ray RMSE measured 1.3% above the FP64 form's, so
-    the bar at this conditioning is 3%."""
-    w = _sample(paper4d, 500)
+    """4-d workload (theta = 0.25, cond K_50 up to ~1e7), checked at the north
+    star's 1% bar, which the FP32 form misses at this conditioning."""
+    w = _sample(paper4d, 2000)
     g = gpu_run(lagp, w, "ray", "fp32", nrays=4)
     o = oracle_run(w, "ray", nrays=4)
-    check_fp32_form(w, g, o, rmse_tol=0.03, max_gap=1e-3)
+    check_fp32_form(w, g, o, rmse_tol=0.01, max_gap=1e-3)
 
 
+@pytest.mark.xfail(reason="FP32 scoring at cond(K) ~1e7: over all 10,000 locations of the 4-d "
+                   "workload the FP32 exhaustive RMSE measured 14% (CUDA-core) and 18% "
+                   "(tensor-core) above the FP64 form's", strict=True)
 @pytest.mark.parametrize("precision", ["fp32", "fp32_tc"])
 def test_fp32_score_exhaustive_paper_scale_4d_sample(lagp, paper4d, precision):
     """On the 4-d workload (theta = 0.25, g = 1e-6, cond K up to ~1e7) FP32
-    scores cannot rank candidates whose v is below ~1e-5: their cancellation
-    error is as large as v.  Over all 10,000 locations the FP32 exhaustive
-    designs measured up to 17% above the FP64 RMSE (the FP64 form is the one
-    for this conditioning); the bar records that limit (25%) and the design
-    checks still hold."""
-    w = _sample(paper4d, 500)
+    scores cannot rank candidates whose v is below ~1e-5: the FP32 correlation
+    values carry errors as large as v.  Checked at the 1% bar, which it misses;
+    the design checks of check_fp32_form run before the RMSE assertion."""
+    w = _sample(paper4d, 2000)
     g = gpu_run(lagp, w, "exhaustive", precision)
     o = oracle_run(w, "exhaustive")
-    check_fp32_form(w, g, o, rmse_tol=0.25, max_gap=None)
+    check_fp32_form(w, g, o, rmse_tol=0.01, max_gap=None)
 
 
 @pytest.fixture(scope="module")
@@ -305,16 +311,34 @@ def large8d():
     return W.large_8d(M=100_000)
 
 
-@pytest.mark.parametrize("search,n,M_or,precision", [("ray", 50, 1500, "fp32"),
-                                                    ("exhaustive", 50, 1500, "fp32"),
-                                                    ("exhaustive", 50, 1500, "fp32_tc"),
-                                                    ("exhaustive", 80, 400, "fp32")])
+_ORACLE_8D = {}
+
+
+def oracle_8d(w, search, n, M_or):
+    """Oracle results on M_or evenly spaced locations of the 8-d workload,
+    computed once per (search, n) and shared by the forms checked against it."""
+    key = (search, n, M_or)
+    if key not in _ORACLE_8D:
+        s = _sample(w, M_or)
+        s.n = n
+        _ORACLE_8D[key] = (s, oracle_run(s, search, nrays=8))
+    return _ORACLE_8D[key]
+
+
+N80 = pytest.mark.xfail(reason="at n = 80 the FP32 exhaustive RMSE measured 1.3% above the "
+                         "oracle's over 5,000 locations", strict=False)
+
+
+@pytest.mark.parametrize("search,n,M_or,precision", [
+    ("ray", 50, 5000, "fp32"), ("exhaustive", 50, 5000, "fp32"),
+    ("exhaustive", 50, 5000, "fp32_tc"),
+    pytest.param("exhaustive", 80, 5000, "fp32", marks=N80)])
 def test_fp32_score_large_8d_sample(lagp, large8d, search, n, M_or, precision):
     """The FP32-scoring form on its own workload (N = 1e6, p = 8, theta = 1)
     in the bench's launch configuration (all 100,000 locations in one call),
-    checked against the oracle on M_or sampled locations: RMSE within 1%.
-    Exhaustive "fp32" runs the incremental CUDA-core scorer, "fp32_tc" the
-    tensor-core contraction (n <= 64)."""
+    checked against the oracle on 5,000 evenly spaced locations: the RMSE
+    ratio's point estimate within 1%.  Exhaustive "fp32" runs the incremental
+    CUDA-core scorer, "fp32_tc" the tensor-core contraction (n <= 64)."""
     import torch
     w = large8d
     out = lagp.predict(to_dev(w.X), to_dev(w.Y), to_dev(w.Xref), w.n0, n, w.nc, w.theta, w.g,
@@ -322,17 +346,17 @@ def test_fp32_score_large_8d_sample(lagp, large8d, search, n, M_or, precision):
     torch.cuda.synchronize()
     idx = np.linspace(0, w.M - 1, M_or).astype(int)
     g = {k: v.cpu().numpy()[idx] for k, v in out.items()}
-    s = _sample(w, M_or)
-    s.n = n
-    o = oracle_run(s, search, nrays=8)
+    s, o = oracle_8d(w, search, n, M_or)
     check_fp32_form(s, g, o, rmse_tol=0.01, max_gap=1e-3 if search == "ray" else None,
                     first_step_gap=1e-3)
 
 
-def test_fp64_large_8d_sample(lagp, large8d):
-    """Plain FP64 form at N = 1e6, p = 8 on 24 locations: bit-identical."""
+@pytest.mark.parametrize("search", ["ray", "exhaustive"])
+def test_fp64_large_8d_sample(lagp, large8d, search):
+    """Plain FP64 form at N = 1e6, p = 8 on 24 locations: bit-identical, for
+    both searches."""
     s = _sample(large8d, 24)
-    g = gpu_run(lagp, s, "ray", "fp64", nrays=8)
-    o = oracle_run(s, "ray", nrays=8)
+    g = gpu_run(lagp, s, search, "fp64", nrays=8)
+    o = oracle_run(s, search, nrays=8)
     ident, _ = assert_fp64_parity(g, o, s.n0, s.M)
     assert ident >= s.M - 1
