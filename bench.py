@@ -490,8 +490,9 @@ def run_nrays_sweep(args, w, tensors, M=20_000, steps=2):
 def run_paper_2d(args, steps=2):
     """The 2-d experiment of Sec 5.1 (201 x 201 grid design on [-2, 2]^2, the
     99 x 99 predictive grid, n = 50, N' = 1000, one ray): locations/s and RMSE
-    of each search and arithmetic form at theta0 = 0.5, then local inference
-    for theta on the FP64 designs (one stage, laGP_mle_predict) and its RMSE.
+    of each search and arithmetic form at theta0 = 0.5; local inference for
+    theta on the FP64 designs in one and two stages (laGP_build_and_predict_mle)
+    with its RMSE; the estimate's kernel alone with its roofline.
     The paper's Table 1 RMSE (0.0009 ray, 0.0010 exhaustive, one stage) is
     context: its nugget and theta start are not stated."""
     import torch
@@ -526,21 +527,48 @@ def run_paper_2d(args, steps=2):
                 raise RuntimeError("device status %d in the 2-d form" % st)
             f = {"locations_per_s": w.M * steps / (e0.elapsed_time(e1) / 1e3),
                  "rmse_theta0": rmse(mean)}
-            if prec == "fp64":
+            if prec == "fp64" and search == "ray":
+                # the local estimate alone, on these designs: its roofline
                 th = torch.empty(w.M, dtype=torch.float64, device=dev)
                 m2 = torch.empty(w.M, dtype=torch.float64, device=dev)
                 v2 = torch.empty(w.M, dtype=torch.float64, device=dev)
+                it = torch.empty(w.M, dtype=torch.int32, device=dev)
                 stt = torch.zeros(1, dtype=torch.int32, device=dev)
                 e0.record()
-                lagp.laGP_mle_predict(X, Y, Xr, sel, w.theta, w.g, 1e-3, 10.0, th, m2, v2, stt)
+                lagp.laGP_mle_predict(X, Y, Xr, sel, w.theta, w.g, 1e-3, 10.0, th, m2, v2, stt,
+                                      iters=it)
                 e1.record()
                 torch.cuda.synchronize()
-                f["mle_stage1"] = {"rmse": rmse(m2), "ms": e0.elapsed_time(e1),
-                                   "theta_median": float(th.median().item()),
-                                   "status": int(stt.item())}
+                ms = e0.elapsed_time(e1)
+                # a Newton iteration evaluates the likelihood and its derivatives:
+                # Cholesky n^3/3, K^{-1} from the factor 2n^3/3, K^{-1} K' 2n^3;
+                # one more evaluation predicts at the estimate
+                flops = float((it.double() + 1).sum().item()) * 3.0 * w.n ** 3
+                out["mle_kernel"] = {
+                    "ms": ms, "locations_per_s": w.M / (ms / 1e3),
+                    "iterations_mean": float(it.double().mean().item()),
+                    "roofline": {"kernel": "mle_theta", "bound": "alu",
+                                 "achieved": flops / (ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                                 "unit": "TFLOP/s",
+                                 "frac": flops / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+                                 "flop_count": "3 n^3 per likelihood evaluation (FP64)"}}
             out["forms"]["%s_%s" % (search, prec)] = f
             del ws
-    out["paper_table1_rmse_context"] = {"ray_n50_stage1": 0.0009, "ext_n50_stage1": 0.0010,
+    # local inference for theta, one call: one stage (design at theta0, estimate)
+    # and two stages (redesign at each location's estimate), FP64 designs
+    for search in ("ray", "exhaustive"):
+        for stages in (1, 2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r = lagp.predict_mle(X, Y, Xr, w.n0, w.n, w.nc, w.theta, w.g, 1e-3, 10.0,
+                                 stages=stages, search=search, nrays=1, precision="fp64")
+            e1.record()
+            torch.cuda.synchronize()
+            out["forms"]["%s_fp64_mle_stage%d" % (search, stages)] = {
+                "locations_per_s": w.M / (e0.elapsed_time(e1) / 1e3), "rmse": rmse(r["mean"]),
+                "theta_median": float(r["theta"].median().item())}
+    out["paper_table1_rmse_context"] = {"ray_n50_stage2": 0.0008, "ext_n50_stage2": 0.0008,
+                                        "ray_n50_stage1": 0.0009, "ext_n50_stage1": 0.0010,
                                         "nn_n50": 0.0023}
     return out
 

@@ -361,17 +361,23 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
           const float ac = Ab[r * PP + c];
           zc[c] = fmaf(s_eval, Eb[r * PP + c] - ac, ac);
         }
+        // paired FP32 arithmetic (two lanes of work per instruction): the
+        // squared distance is summed as even and odd coordinates, then added
+        float2 nz[PP / 2];
+#pragma unroll
+        for (int c = 0; c < PP; c += 2) nz[c / 2] = make_float2(-zc[c], -zc[c + 1]);
         for (int k = q; k < j; k += G) {
           const float* sk = Sf + k * PP;
-          float d = 0.f;
+          float2 d2 = make_float2(0.f, 0.f);
 #pragma unroll
           for (int c = 0; c < PP; c += 4) {
             const float4 s4 = *reinterpret_cast<const float4*>(sk + c);
-            float t0 = s4.x - zc[c], t1 = s4.y - zc[c + 1], t2 = s4.z - zc[c + 2],
-                  t3 = s4.w - zc[c + 3];
-            d = fmaf(t0, t0, d); d = fmaf(t1, t1, d); d = fmaf(t2, t2, d); d = fmaf(t3, t3, d);
+            const float2 t01 = __fadd2_rn(make_float2(s4.x, s4.y), nz[c / 2]);
+            const float2 t23 = __fadd2_rn(make_float2(s4.z, s4.w), nz[c / 2 + 1]);
+            d2 = __ffma2_rn(t01, t01, d2);
+            d2 = __ffma2_rn(t23, t23, d2);
           }
-          kzr[k] = __expf(d * nit);
+          kzr[k] = __expf((d2.x + d2.y) * nit);
         }
       }
       __syncwarp();
@@ -380,14 +386,16 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
         for (int i = q; i < j; i += G) {
           const float* Li = Lf + roff(i);
           const int len = (i + 4) & ~3;
-          float w0 = 0.f, w1 = 0.f;
+          // two accumulators (elements 0, 2 and 1, 3 of each quad) in one
+          // paired FMA per element pair
+          float2 acc = make_float2(0.f, 0.f);
           for (int k = 0; k < len; k += 4) {
             const float4 l4 = *reinterpret_cast<const float4*>(Li + k);
             const float4 k4 = *reinterpret_cast<const float4*>(kzr + k);
-            w0 = fmaf(l4.x, k4.x, w0); w1 = fmaf(l4.y, k4.y, w1);
-            w0 = fmaf(l4.z, k4.z, w0); w1 = fmaf(l4.w, k4.w, w1);
+            acc = __ffma2_rn(make_float2(l4.x, l4.y), make_float2(k4.x, k4.y), acc);
+            acc = __ffma2_rn(make_float2(l4.z, l4.w), make_float2(k4.z, k4.w), acc);
           }
-          const float w = w0 + w1;
+          const float w = acc.x + acc.y;
           vs = fmaf(w, w, vs);
           ns = fmaf(w, zf[i], ns);
         }
@@ -447,9 +455,9 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
     // ---- snap: nearest allowed unselected candidate (ties to the lower rank) ----
     // allowed: not one of this step's ray starts unless it coincides with x*;
     // if no candidate is allowed, the nearest unselected one (second pair)
-    float xr[PP];
+    float2 nx[PP / 2];
 #pragma unroll
-    for (int k = 0; k < PP; ++k) xr[k] = xs[k];
+    for (int k = 0; k < PP; k += 2) nx[k / 2] = make_float2(-xs[k], -xs[k + 1]);
     float bd0 = __int_as_float(0x7f800000), bd1 = bd0;
     int bi0 = 0x7fffffff, bi1 = 0x7fffffff;
     {
@@ -460,16 +468,18 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
         const int rr = wd * 32 + lane;
         if (rr < nc && !(mask[wd] & bit)) {
           const float* c = P.Xf + (int64_t)cl[rr] * PP;
-          bool same = true;
-          float d = 0.f;
+          float2 d2 = make_float2(0.f, 0.f);
+          bool same = true;                   // every coordinate equal to x*'s
 #pragma unroll
           for (int k = 0; k < PP; k += 4) {
             const float4 cv = *reinterpret_cast<const float4*>(c + k);
-            float t = cv.x - xr[k]; same &= (t == 0.f); d = fmaf(t, t, d);
-            t = cv.y - xr[k + 1]; same &= (t == 0.f); d = fmaf(t, t, d);
-            t = cv.z - xr[k + 2]; same &= (t == 0.f); d = fmaf(t, t, d);
-            t = cv.w - xr[k + 3]; same &= (t == 0.f); d = fmaf(t, t, d);
+            const float2 t01 = __fadd2_rn(make_float2(cv.x, cv.y), nx[k / 2]);
+            const float2 t23 = __fadd2_rn(make_float2(cv.z, cv.w), nx[k / 2 + 1]);
+            same &= (t01.x == 0.f) & (t01.y == 0.f) & (t23.x == 0.f) & (t23.y == 0.f);
+            d2 = __ffma2_rn(t01, t01, d2);
+            d2 = __ffma2_rn(t23, t23, d2);
           }
+          const float d = d2.x + d2.y;
           if (d < bd1) { bd1 = d; bi1 = rr; }
           if ((same || !(smask[wd] & bit)) && d < bd0) { bd0 = d; bi0 = rr; }
         }

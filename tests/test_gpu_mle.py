@@ -134,33 +134,43 @@ def test_bad_index_and_largest_design(lagp):
 def test_one_call_stages_match_the_oracle(lagp, name, search):
     """laGP_build_and_predict_mle: the design, the estimate and, for two
     stages, the redesign at each location's own estimate, all in one call
-    (per-location theta inside the design kernels), against the oracle's
-    predict_mle.  Stage 1 designs are identical (FP64 form) and the estimate
-    agrees to 1e-8.  A stage-2 design is built at the GPU's own estimate,
-    which differs from the oracle's in the eighth digit, so a near-tie may
-    send it elsewhere; most locations must still match exactly."""
+    (per-location theta inside the design kernels).
+    Stage 1 against the oracle's predict_mle: identical designs (FP64 form),
+    the estimate to 1e-8.  Stage 2 redesigns at the GPU's own first estimate,
+    which differs from the oracle's in the eighth digit -- at these workloads
+    a relative change of theta that small already moves most greedy designs
+    (the oracle's rounding-noise runs move them with 1 ulp) -- so stage 2 is
+    checked against the oracle's design at the GPU's first estimate, location
+    by location: identical designs, then the estimate on it started there."""
     w = W.dense_2d() if name == "dense_2d" else W.paper_2d(M=24)
     Xref = w.Xref[:24]
     nr = 1 if name == "paper_2d" else 2
     X, Y, Xr = to_dev(w.X), to_dev(w.Y), to_dev(Xref)
     tmax = 10.0 if name == "paper_2d" else TMAX
-    for stages in (1, 2):
-        g_out = lagp.predict_mle(X, Y, Xr, w.n0, w.n, w.nc, w.theta, w.g, TMIN, tmax,
-                                 stages=stages, search=search, nrays=nr, precision="fp64",
-                                 want_selected=True)
-        o = oracle.predict_mle(w.X, w.Y, Xref, w.n0, w.n, w.nc, w.theta, w.g, TMIN, tmax,
-                               search=search, nrays=nr, stages=stages, nthreads=0)
-        sel = g_out["selected"].cpu().numpy()
-        same = np.all(sel == o["selected"], axis=1)
-        if stages == 1:
-            assert same.all()
-        else:
-            assert same.mean() >= 0.9, same.mean()
-        th = g_out["theta"].cpu().numpy()
-        np.testing.assert_allclose(th[same], o["theta"][same], rtol=1e-8)
-        mean, s2 = g_out["mean"].cpu().numpy(), g_out["s2"].cpu().numpy()
-        for m in np.nonzero(same)[0]:
-            rel, s2_err = _cond_bounds(w.X, w.Y, o["selected"][m], Xref[m], o["theta"][m], w.g)
-            mo, so = o["mean"][m], o["s2"][m]
-            assert abs(mean[m] - mo) <= rel * max(1.0, abs(mo)) + 1e-7 * abs(mo) + 1e-10, m
-            assert abs(s2[m] - so) <= s2_err + 1e-7 * abs(so), m
+    run = lambda stages: lagp.predict_mle(X, Y, Xr, w.n0, w.n, w.nc, w.theta, w.g, TMIN, tmax,
+                                          stages=stages, search=search, nrays=nr,
+                                          precision="fp64", want_selected=True)
+    g1, g2 = run(1), run(2)
+    o1 = oracle.predict_mle(w.X, w.Y, Xref, w.n0, w.n, w.nc, w.theta, w.g, TMIN, tmax,
+                            search=search, nrays=nr, stages=1, nthreads=0)
+    np.testing.assert_array_equal(g1["selected"].cpu().numpy(), o1["selected"])
+    th1 = g1["theta"].cpu().numpy()
+    np.testing.assert_allclose(th1, o1["theta"], rtol=1e-8)
+    sel2 = g2["selected"].cpu().numpy()
+    th2, mean2, s22 = (g2[k].cpu().numpy() for k in ("theta", "mean", "s2"))
+    for m in range(len(Xref)):
+        d = oracle.predict(w.X, w.Y, Xref[m:m + 1], w.n0, w.n, w.nc, float(th1[m]), w.g, search,
+                           nrays=nr)
+        np.testing.assert_array_equal(sel2[m], d["selected"][0])
+        S, yS = w.X[sel2[m]], w.Y[sel2[m]]
+        t2, _ = oracle.mle_theta(S, yS, float(th1[m]), w.g, TMIN, tmax)
+        assert abs(th2[m] - t2) <= 1e-8 * t2, (m, th2[m], t2)
+        rel, s2_err = _cond_bounds(w.X, w.Y, sel2[m], Xref[m], t2, w.g)
+        # the prediction at the GPU's estimate against numpy kriging there
+        from scipy.spatial.distance import cdist
+        K = np.exp(-cdist(S, S, "sqeuclidean") / th2[m]) + w.g * np.eye(len(S))
+        k = np.exp(-cdist(S, Xref[m][None], "sqeuclidean") / th2[m])[:, 0]
+        mu = k @ np.linalg.solve(K, yS)
+        v = (yS @ np.linalg.solve(K, yS)) * ((1 + w.g) - k @ np.linalg.solve(K, k)) / len(S)
+        assert abs(mean2[m] - mu) <= rel * max(1.0, abs(mu)) + 1e-10, m
+        assert abs(s22[m] - v) <= s2_err + 1e-9 * abs(v), m
