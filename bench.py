@@ -60,6 +60,11 @@ def parse():
                     help="skip the serving form (request stream over a serving context)")
     ap.add_argument("--serve-seconds", type=float, default=4.0,
                     help="arrival window per rate of the serving form")
+    ap.add_argument("--workload", default="sinusoid_8d", choices=["sinusoid_8d", "paper_2d"],
+                    help="the timed workload: the 8-d headline or the 2-d grid of Sec 5.1")
+    ap.add_argument("--mle-stages", type=int, default=0, choices=[0, 1, 2],
+                    help="time designs coupled with local inference for theta (one or two "
+                         "stages) instead of designs at a fixed theta")
     return ap.parse_args()
 
 
@@ -105,12 +110,15 @@ def shard(M_total, rank, world):
     return lo, lo + per + (1 if rank < extra else 0)
 
 
-def rank_workload(M, N, rank, world):
+def rank_workload(M, N, rank, world, name="sinusoid_8d"):
     """The workload of one rank (weak scaling, M locations per rank): every
     rank draws the same design, responses and job-wide location set (seed 0,
     M * world locations) and keeps its own block of them."""
     from paper_1409_0074_gb300 import workloads as W
-    w = W.large_8d(M=M * world, N=N)
+    if name == "paper_2d":
+        w = W.paper_2d(M=min(M * world, 9801))
+    else:
+        w = W.large_8d(M=M * world, N=N)
     lo, hi = shard(w.M, rank, world)
     w.Xref, w.Ytrue, w.M = w.Xref[lo:hi], w.Ytrue[lo:hi], hi - lo
     return w
@@ -317,7 +325,7 @@ def run_ours(args, rank, world):
     from paper_1409_0074_gb300 import lagp
 
     dev = torch.device("cuda", torch.cuda.current_device())
-    w = rank_workload(args.M, args.N, rank, world)
+    w = rank_workload(args.M, args.N, rank, world, args.workload)
     N, p, M = w.N, w.p, w.M
     s, pr = lagp.SEARCH[args.search], lagp.PRECISION[args.precision]
     R = w.nrays
@@ -329,10 +337,20 @@ def run_ours(args, rank, world):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
+    if args.mle_stages:
+        wsb = lagp.laGP_mle_workspace_bytes(N, p, M, w.n, w.nc, R, s, pr)
+        ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        theta_hat = torch.empty(M, dtype=torch.float64, device=dev)
+
     def step():
         flush.zero_()
-        lagp.laGP_build_and_predict(X, Y, Xr, w.n0, w.n, w.nc, w.theta, w.g, s, R, pr, mean, s2,
-                                    ws, stream=stream)
+        if args.mle_stages:
+            lagp.laGP_build_and_predict_mle(X, Y, Xr, w.n0, w.n, w.nc, w.theta, w.g, 1e-3, 10.0,
+                                            args.mle_stages, s, R, pr, theta_hat, mean, s2, ws,
+                                            stream=stream)
+        else:
+            lagp.laGP_build_and_predict(X, Y, Xr, w.n0, w.n, w.nc, w.theta, w.g, s, R, pr, mean,
+                                        s2, ws, stream=stream)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -370,13 +388,15 @@ def run_ours(args, rank, world):
     ev = {k: v / chunks for k, v in eval_sums(nev, w.n0).items()}
     roof = roofline(name, tot_ms, launches, w, M / chunks, ev,
                     traffic_ok=(w.M == 100_000 and w.N == 1_000_000 and chunks == 1))
+    if args.mle_stages:
+        roof = None       # several kernel kinds share the step; see the kernel times
     kernels = {k: {"ms_per_step": v[0] / args.steps, "launches": v[1],
                    "share": v[0] / sum(x[0] for x in prof.values())} for k, v in prof.items()}
     mean_evals = float(nev.sum(axis=1).mean() / (w.n - w.n0))
     return dict(value=value, ms=ms_max, clocks=clk.summary(), roofline=roof, kernels=kernels,
                 gpu_launches=int(sum(v[1] for v in prof.values())), w=w, tensors=(X, Y, Xr),
                 evals_per_step=mean_evals, max_evals_per_step=float(nev.max()),
-                rmse=float(np.sqrt(np.mean((trace["mean"].cpu().numpy() - w.Ytrue) ** 2))))
+                rmse=float(np.sqrt(np.mean((mean.cpu().numpy() - w.Ytrue) ** 2))))
 
 
 def run_e2e(args, w):
@@ -743,7 +763,12 @@ def run_cpu_baseline(args, w, search, sample=None, one_core=False):
 
 
 def base_line(args, world, value, ms, w):
-    return {"metric": "locations/sec at N=1e6,d=8,n=50 (%s search)" % args.search, "value": value,
+    metric = ("locations/sec at N=1e6,d=8,n=50 (%s search)" % args.search
+              if args.workload == "sinusoid_8d" else
+              "locations/sec, 2-d grid of Sec 5.1, n=50 (%s search)" % args.search)
+    if args.mle_stages:
+        metric += ", local theta in %d stage(s)" % args.mle_stages
+    return {"metric": metric, "value": value,
             "unit": "locations/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps if ms is not None else None,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

@@ -29,6 +29,10 @@
 // quarter overflowed; otherwise it is marked for the streaming kernel's exact
 // pass (threshold infinity).  knn_finalize joins the quarters and keeps the
 // entries within the N'-th smallest + 2 err for the exact ranking.
+// A batch with fewer location tiles than SMs splits the design into segments,
+// one CTA each (grid y); the segments of a location append to its buffer
+// through a global counter (passes are rare), and knn_tc_join decides its
+// validity once all of them are done.  The buffered set is the same.
 //
 // err bounds |d_tc - d64| for the 3xTF32 contraction: operand splitting
 // (3 * 2^-22 |A_k B_k| per term), FP32 accumulation over 3K products
@@ -175,7 +179,7 @@ knn_tc(const float* __restrict__ Btiles, int64_t ntiles, int p, const double* __
        int64_t M, const double* __restrict__ center, const unsigned* __restrict__ maxn2_bits,
        int nc_max, const int32_t* __restrict__ nc_loc, int cap, const float* __restrict__ pilot,
        KnnEntry* __restrict__ buf, int32_t* __restrict__ cnt_out, int32_t* __restrict__ seg_out,
-       unsigned* __restrict__ status) {
+       unsigned* __restrict__ status, int split) {
   using L = KtSmem<KA>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
@@ -195,6 +199,10 @@ knn_tc(const float* __restrict__ Btiles, int64_t ntiles, int p, const double* __
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t q0 = (int64_t)blockIdx.x * KT_M;
+  // design segment of this CTA: tiles [t_lo, t_lo + nt) (the whole design
+  // unless the launch splits it over gridDim.y CTAs per location tile)
+  const int64_t t_lo = (int64_t)blockIdx.y * ntiles / gridDim.y;
+  const int64_t nt = (int64_t)(blockIdx.y + 1) * ntiles / gridDim.y - t_lo;
   const float rdes = sqrtf(__uint_as_float(*maxn2_bits)) * 1.0001f;
   const float inf = __int_as_float(0x7f800000);
 
@@ -259,7 +267,7 @@ knn_tc(const float* __restrict__ Btiles, int64_t ntiles, int p, const double* __
     // ---------------- producer ----------------
     if (lane == 0) {
       int64_t issued = 0;
-      for (int64_t t = 0; t < ntiles; ++t) {
+      for (int64_t t = 0; t < nt; ++t) {
         const int s = (int)(t % KT_STAGES);
         if (t >= KT_STAGES) {
           if (*abort_v || !mbar_wait(&empty[s], (uint32_t)(((t / KT_STAGES) - 1) & 1))) {
@@ -268,8 +276,8 @@ knn_tc(const float* __restrict__ Btiles, int64_t ntiles, int p, const double* __
           }
         }
         mbar_expect_tx(&full[s], L::STAGE_BYTES);
-        bulk_g2s(smem + L::S_OFF + s * L::STAGE_BYTES, Btiles + t * (int64_t)(L::STAGE_BYTES / 4),
-                 L::STAGE_BYTES, &full[s]);
+        bulk_g2s(smem + L::S_OFF + s * L::STAGE_BYTES,
+                 Btiles + (t_lo + t) * (int64_t)(L::STAGE_BYTES / 4), L::STAGE_BYTES, &full[s]);
         issued = t + 1;
       }
       if (*abort_v) {   // copies in flight land before the CTA can exit
@@ -285,7 +293,7 @@ knn_tc(const float* __restrict__ Btiles, int64_t ntiles, int p, const double* __
       const uint32_t sbo = (KA / 4) * 128;
       const uint32_t a_hi = smem_u32(Ahi), a_lo = smem_u32(Alo);
       int64_t committed = 0;
-      for (int64_t t = 0; t < ntiles; ++t) {
+      for (int64_t t = 0; t < nt; ++t) {
         const int s = (int)(t % KT_STAGES), b = (int)(t % KT_GROUPS);
         bool ok = !*abort_v && mbar_wait(&full[s], (uint32_t)((t / KT_STAGES) & 1));
         if (ok && t >= KT_GROUPS)
@@ -321,7 +329,7 @@ knn_tc(const float* __restrict__ Btiles, int64_t ntiles, int p, const double* __
     const int seg = cap / KT_GROUPS;                       // this group's quarter of the buffer
     KnnEntry* qb = buf + q * (int64_t)cap + g * seg;
     int mycnt = 0, mybelow = 0;
-    for (int64_t t = g; t < ntiles; t += KT_GROUPS) {
+    for (int64_t t = g; t < nt; t += KT_GROUPS) {
       const bool ok = !*abort_v && mbar_wait(&tfull[g], (uint32_t)((t / KT_GROUPS) & 1));
       if (!__all_sync(0xffffffffu, ok)) *abort_v = 1;
       if (*abort_v) {
@@ -331,7 +339,7 @@ knn_tc(const float* __restrict__ Btiles, int64_t ntiles, int p, const double* __
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int32_t pbase = (int32_t)(t * KT_N);
+      const int32_t pbase = (int32_t)((t_lo + t) * KT_N);
 #pragma unroll 1
       for (int c0 = 0; c0 < KT_N; c0 += 64) {
         // two 32-column loads, one wait
@@ -345,10 +353,14 @@ knn_tc(const float* __restrict__ Btiles, int64_t ntiles, int p, const double* __
         for (int u = 0; u < 64; ++u) {
           const float d = __uint_as_float(v[u]);
           if (d <= keep) {
-            if (mycnt < seg) {
-              KnnEntry e;
-              e.d = fmaxf(d, 0.f);
-              e.idx = pbase + c0 + u;
+            KnnEntry e;
+            e.d = fmaxf(d, 0.f);
+            e.idx = pbase + c0 + u;
+            if (split) {
+              // segments of one location share its buffer through a counter
+              const int slot = atomicAdd(&seg_out[q * KT_GROUPS], 1);
+              if (slot < cap) buf[q * (int64_t)cap + slot] = e;
+            } else if (mycnt < seg) {
               qb[mycnt] = e;
             }
             ++mycnt;
@@ -360,7 +372,11 @@ knn_tc(const float* __restrict__ Btiles, int64_t ntiles, int p, const double* __
     cnt_sm[g * KT_M + c] = mycnt;
     atomicAdd(&below_sm[c], mybelow);
     kt_epi_barrier();
-    if (g == 0 && q < M) {
+    if (split) {
+      // the location's totals come together in knn_tc_join once every
+      // segment is done
+      if (g == 0 && q < M && below_sm[c] > 0) atomicAdd(&seg_out[q * KT_GROUPS + 1], below_sm[c]);
+    } else if (g == 0 && q < M) {
       const int nc = nc_loc ? nc_loc[q] : nc_max;
       int n = 0;
       bool over = false;
@@ -381,6 +397,26 @@ knn_tc(const float* __restrict__ Btiles, int64_t ntiles, int p, const double* __
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(taddr));
   }
+}
+
+// After a split launch: a location is valid when its buffer did not overflow
+// and at least N' of its entries lie at or below the pilot value; its entries
+// are then the first count of the buffer (one quarter, as finalize reads it).
+__global__ void knn_tc_join(int64_t M, int nc_max, const int32_t* __restrict__ nc_loc, int cap,
+                            const float* __restrict__ pilot, int32_t* __restrict__ cnt,
+                            int32_t* __restrict__ seg, const unsigned* __restrict__ status) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= M) return;
+  const int total = seg[q * KT_GROUPS], below = seg[q * KT_GROUPS + 1];
+  const int nc = nc_loc ? nc_loc[q] : nc_max;
+  const bool thr_ok = pilot[q] < __int_as_float(0x7f800000);
+  // after a timed-out stream (status already set) nothing of it is kept
+  cnt[q] = (*status & LAGP_DEV_TIMEOUT) ? 0
+                                        : ((total <= cap && below >= nc && thr_ok) ? total : -1);
+  seg[q * KT_GROUPS] = total <= cap ? total : cap;
+  seg[q * KT_GROUPS + 1] = 0;
+  seg[q * KT_GROUPS + 2] = 0;
+  seg[q * KT_GROUPS + 3] = 0;
 }
 
 // Keep, per valid location, the buffered entries within the N'-th smallest
@@ -444,6 +480,21 @@ cudaError_t launch_knn_tc(int64_t Npad, int p, const double* xref, int64_t M, in
   const unsigned grid = (unsigned)((M + KT_M - 1) / KT_M);
   KnnEntry* kbuf = reinterpret_cast<KnnEntry*>(ws.knn_buf);
   cudaError_t err;
+  // A small batch has fewer location tiles than SMs: split the design into
+  // segments so that about two CTAs per SM run, each segment at least 64 tiles.
+  int sms = 0, dev = 0;
+  if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+  if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return err;
+  int64_t nseg = (2 * (int64_t)sms + grid - 1) / grid;
+  if (nseg > ntiles / 64) nseg = ntiles / 64;
+  if (nseg > 65535) nseg = 65535;
+  if (nseg < 1) nseg = 1;
+  const int split = nseg > 1 ? 1 : 0;
+  if (split && (err = cudaMemsetAsync(ws.knn_seg, 0, sizeof(int32_t) * KT_GROUPS * M, s)) !=
+                   cudaSuccess)
+    return err;
+  const dim3 g3(grid, (unsigned)nseg);
   switch (KA) {
 #define KT_CASE(V)                                                                              \
   case V: {                                                                                     \
@@ -451,9 +502,9 @@ cudaError_t launch_knn_tc(int64_t Npad, int p, const double* xref, int64_t M, in
     err = cudaFuncSetAttribute(knn_tc<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
     if (err != cudaSuccess) return err;                                                         \
     prof_begin("knn_tc", s);                                                                    \
-    knn_tc<V><<<grid, KT_THREADS, sm, s>>>(ws.Btc, ntiles, p, xref, M, ws.center, ws.maxn2,     \
-                                           nc_max, nc_loc, cap, ws.knn_thr, kbuf, ws.knn_cnt,   \
-                                           ws.knn_seg, ws.status);                              \
+    knn_tc<V><<<g3, KT_THREADS, sm, s>>>(ws.Btc, ntiles, p, xref, M, ws.center, ws.maxn2,       \
+                                         nc_max, nc_loc, cap, ws.knn_thr, kbuf, ws.knn_cnt,     \
+                                         ws.knn_seg, ws.status, split);                         \
     prof_end(s);                                                                                \
     break;                                                                                      \
   }
@@ -463,6 +514,12 @@ cudaError_t launch_knn_tc(int64_t Npad, int p, const double* xref, int64_t M, in
 #undef KT_CASE
     default:
       return cudaErrorInvalidValue;
+  }
+  if (split) {
+    prof_begin("knn_tc_join", s);
+    knn_tc_join<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(M, nc_max, nc_loc, cap, ws.knn_thr,
+                                                              ws.knn_cnt, ws.knn_seg, ws.status);
+    prof_end(s);
   }
   prof_begin("knn_finalize", s);
   knn_finalize<<<(unsigned)((M + 7) / 8), 256, 0, s>>>(xref, M, p, KA, ws.center, ws.maxn2,
