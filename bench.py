@@ -713,15 +713,15 @@ def run_serving(args, rates32=(50.0, 200.0, 400.0, 600.0, 800.0, 1000.0, 1400.0)
     w = W.large_8d(M=1)
     dev = torch.device("cuda", torch.cuda.current_device())
     X, Y = torch.from_numpy(w.X).to(dev), torch.from_numpy(w.Y).to(dev)
-    slots, max_batch = 8, 4096
+    slots, max_batch, arena_gb = 8, 32768, 24
     rng = np.random.default_rng(11)
     out = {"design": "sinusoid_8d_N1000000", "request_sizes": "log-uniform 1..4096",
            "n": [30, 50, 100], "N_close": 1000, "search": "ray", "nrays": 8, "slots": slots,
-           "max_batch": max_batch, "arena_gb": 8}
+           "max_batch": max_batch, "arena_gb": arena_gb}
     for prec, rates, secs in (("fp32", rates32, args.serve_seconds),
                               ("fp64", rates64, 2 * args.serve_seconds)):
         ctx = lagp.Context(X, Y, w.theta, w.g, w.n0, 1000, lagp.LAGP_RAY, 8,
-                           lagp.PRECISION[prec], 8 << 30, max_inflight=slots)
+                           lagp.PRECISION[prec], arena_gb << 30, max_inflight=slots)
         # warm-up (kernel load, tune table)
         srv = Server(CtxBackend(ctx, max_batch, slots), max_batch)
         run_stream(srv, poisson_requests(rng, 50.0, 6, w.p, sizes=(1, 256)))

@@ -60,6 +60,8 @@ def _configure(L):
     dp, ip = C.POINTER(C.c_double), C.POINTER(C.c_int32)
     L.lagp_oracle_set_jitter.restype = None
     L.lagp_oracle_set_jitter.argtypes = [C.c_uint64]
+    L.lagp_oracle_set_snap_scope.restype = None
+    L.lagp_oracle_set_snap_scope.argtypes = [C.c_int]
     L.lagp_oracle_exp.restype = C.c_double
     L.lagp_oracle_exp.argtypes = [C.c_double]
     L.lagp_oracle_sqdist.restype = C.c_double
@@ -205,12 +207,31 @@ def bbox(X):
 SEARCH = {"exhaustive": 0, "ray": 1}
 
 
+SNAP = {"candidates": 0, "design": 1}
+
+
+@contextlib.contextmanager
+def _snap_scope(snap):
+    lib().lagp_oracle_set_snap_scope(SNAP[snap])
+    try:
+        yield
+    finally:
+        lib().lagp_oracle_set_snap_scope(0)
+
+
 def predict(X, Y, Xref, n0, n, nc, theta, g, search="exhaustive", nrays=0,
-            n_arr=None, nc_arr=None, nthreads=1):
+            n_arr=None, nc_arr=None, nthreads=1, snap="candidates"):
     """The whole path for every row of Xref.  Returns a dict with mean, s2,
     selected (design indices in selection order, -1 padded), gap (per greedy
     step, smallest relative gap of its decisions), nevals (ALC evaluations per
-    ray step), status, and threads (OpenMP threads used)."""
+    ray step), status, and threads (OpenMP threads used).  snap = "design"
+    snaps ray steps over all of X_N outside the design (reading R14) instead
+    of the unselected candidates."""
+    with _snap_scope(snap):
+        return _predict(X, Y, Xref, n0, n, nc, theta, g, search, nrays, n_arr, nc_arr, nthreads)
+
+
+def _predict(X, Y, Xref, n0, n, nc, theta, g, search, nrays, n_arr, nc_arr, nthreads):
     X, pX = _d(X)
     Y, pY = _d(Y)
     Xref, pR = _d(np.atleast_2d(Xref))
@@ -261,7 +282,7 @@ def mle_theta(S, y, theta0, g, tmin, tmax, tol=1e-10, maxit=200):
 
 
 def predict_mle(X, Y, Xref, n0, n, nc, theta0, g, tmin, tmax, search="exhaustive", nrays=0,
-                stages=1, nthreads=1):
+                stages=1, nthreads=1, snap="candidates"):
     """Local designs coupled with local inference for theta: `stages` rounds of
     (greedy design at the current theta, then the MLE on that design, starting
     from theta0), and the predictive equations at the last estimate on the last
@@ -276,8 +297,9 @@ def predict_mle(X, Y, Xref, n0, n, nc, theta0, g, tmin, tmax, search="exhaustive
     th, pt = _d(np.zeros(M))
     sel, psel = _i(np.zeros((M, n), np.int32))
     st, pst = _i(np.zeros(M, np.int32))
-    used = lib().lagp_oracle_predict_mle(pX, pY, N, p, pR, M, n0, n, nc, float(theta0),
-                                         float(g), float(tmin), float(tmax), SEARCH[search],
-                                         int(nrays), int(stages), pm, ps, pt, psel, pst,
-                                         int(nthreads))
+    with _snap_scope(snap):
+        used = lib().lagp_oracle_predict_mle(pX, pY, N, p, pR, M, n0, n, nc, float(theta0),
+                                             float(g), float(tmin), float(tmax), SEARCH[search],
+                                             int(nrays), int(stages), pm, ps, pt, psel, pst,
+                                             int(nthreads))
     return dict(mean=mean, s2=s2, theta=th, selected=sel, status=st, threads=used)

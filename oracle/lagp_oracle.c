@@ -40,6 +40,12 @@
  *   R12 K_{n0}^{-1} is built by n0 partitioned-inverse steps from the empty
  *       design, the same update the greedy loop uses.
  *   R13 the variance output is sigma^2 of Eq. preds2 with df = n.
+ *   R14 (unlimited ray scope, off by default; lagp_oracle_set_snap_scope(1))
+ *       the snap of R11 searches all of X_N minus the current design instead
+ *       of the unselected candidates (Sec 5 places no N' limit on rays): the
+ *       nearest such point to x*, ray starts of the step forbidden unless
+ *       equal to x*; ties go to the point nearer to x, then the lower index.
+ *       Ray starts still come from the N' candidates.
  */
 #include <math.h>
 #include <stdint.h>
@@ -390,9 +396,19 @@ typedef struct {
     double* kx;           /* n: k_j(x)                      */
     double* work;         /* 4n + 4p doubles                */
     unsigned char* used;  /* nc flags                       */
-    int32_t* sel;         /* n selected ranks               */
+    int32_t* sel;         /* n selected ranks (-1: not a candidate) */
+    int32_t* gsel;        /* n selected design indices      */
+    const double* X;      /* the design X_N (N x p)         */
+    int64_t N;
+    const int32_t* cidx;  /* nc candidate design indices    */
+    unsigned char* gused; /* N flags of the design, or NULL (candidate scope) */
     int j;                /* current design size            */
 } loc_t;
+
+/* Scope of the ray search's snap (R11 / R14): 0 the unselected candidates,
+   1 all of X_N outside the current design. */
+static int g_snap_scope = 0;
+void lagp_oracle_set_snap_scope(int scope) { g_snap_scope = scope; }
 
 typedef struct { loc_t* L; const double* A; const double* E; double* z; double* work; } rayfun_t;
 
@@ -405,11 +421,12 @@ static double ray_negalc(double s, void* vctx)
                             L->theta, L->g, c->work, NULL, NULL);
 }
 
-/* Adds candidate rank r to the design (update, Sec 2.2). Returns v. */
-static double add_point(loc_t* L, int r)
+/* Adds design point gi (candidate rank r, or -1 when it is not a candidate)
+   to the design (update, Sec 2.2). Returns v. */
+static double add_point_g(loc_t* L, int64_t gi, int r)
 {
     const int p = L->p, j = L->j;
-    const double* c = L->cx + (size_t)r * p;
+    const double* c = L->X + gi * p;
     double* kvec = L->work + 2 * L->n;
     for (int i = 0; i < j; ++i) kvec[i] = corr(L->S + i * p, c, p, L->theta);
     double v = lagp_oracle_update(L->Kinv, j, L->n, kvec, L->g, L->work);
@@ -417,9 +434,21 @@ static double add_point(loc_t* L, int r)
     memcpy(L->S + (size_t)j * p, c, sizeof(double) * p);
     L->kx[j] = corr(c, L->x, p, L->theta);
     L->sel[j] = r;
-    L->used[r] = 1;
+    L->gsel[j] = (int32_t)gi;
+    if (r >= 0) L->used[r] = 1;
+    if (L->gused) L->gused[gi] = 1;
     L->j = j + 1;
     return v;
+}
+
+/* Adds candidate rank r to the design. */
+static double add_point(loc_t* L, int r) { return add_point_g(L, L->cidx[r], r); }
+
+/* Candidate rank of design point gi, or -1. */
+static int rank_of(const loc_t* L, int64_t gi)
+{
+    for (int r = 0; r < L->nc; ++r) if (L->cidx[r] == gi) return r;
+    return -1;
 }
 
 /* Exhaustive search over unselected candidates (Sec 2.2). */
@@ -439,8 +468,9 @@ static int search_exhaustive(loc_t* L, double* gap)
     return rbest;
 }
 
-/* Ray search (Sec 4) with R rays; returns the chosen rank. */
-static int search_ray(loc_t* L, int R, double* gap, int* nevals_out)
+/* Ray search (Sec 4) with R rays; returns the chosen design index and its
+   candidate rank in *rank_out (-1 when the snap left the candidates). */
+static int64_t search_ray(loc_t* L, int R, double* gap, int* nevals_out, int* rank_out)
 {
     const int p = L->p;
     int* U = (int*)malloc(sizeof(int) * (size_t)L->nc);
@@ -498,8 +528,40 @@ static int search_ray(loc_t* L, int R, double* gap, int* nevals_out)
 
     /* snap: nearest unselected candidate, ray starts forbidden unless equal to x* */
     int rbest = -1;
+    int64_t gbest = -1;
     double d1 = INFINITY, d2 = INFINITY;
-    for (int u = 0; u < nU; ++u) {
+    if (L->gused) {
+        /* R14: the nearest point of X_N outside the design */
+        double dxb = INFINITY;
+        for (int pass = 0; pass < 2 && gbest < 0; ++pass) {
+            for (int64_t c = 0; c < L->N; ++c) {
+                if (L->gused[c]) continue;
+                const double* cc = L->X + c * p;
+                if (pass == 0) {
+                    int forbidden = 0;
+                    for (int i = 0; i < R; ++i) {
+                        if (L->cidx[starts[i]] != c) continue;
+                        int same = 1;
+                        for (int k = 0; k < p; ++k) if (cc[k] != xs[k]) { same = 0; break; }
+                        if (!same) forbidden = 1;
+                    }
+                    if (forbidden) continue;
+                }
+                double d = lagp_oracle_sqdist(cc, xs, p);
+                if (d < d1) {
+                    d2 = d1; d1 = d; gbest = c; dxb = lagp_oracle_sqdist(cc, L->x, p);
+                } else if (d == d1) {
+                    d2 = d;
+                    double dx = lagp_oracle_sqdist(cc, L->x, p);
+                    if (dx < dxb) { gbest = c; dxb = dx; }
+                } else if (d < d2) {
+                    d2 = d;
+                }
+            }
+        }
+        rbest = rank_of(L, gbest);
+    }
+    for (int u = 0; u < nU && !L->gused; ++u) {
         int r = U[u];
         const double* c = L->cx + (size_t)r * p;
         int forbidden = 0;
@@ -514,7 +576,7 @@ static int search_ray(loc_t* L, int R, double* gap, int* nevals_out)
         if (d < d1) { d2 = d1; d1 = d; rbest = r; }
         else if (d < d2) d2 = d;
     }
-    if (rbest < 0) {               /* every unselected point is a start: snap over U */
+    if (rbest < 0 && !L->gused) {  /* every unselected point is a start: snap over U */
         for (int u = 0; u < nU; ++u) {
             double d = lagp_oracle_sqdist(L->cx + (size_t)U[u] * p, xs, p);
             if (d < d1) { d2 = d1; d1 = d; rbest = U[u]; }
@@ -528,7 +590,9 @@ static int search_ray(loc_t* L, int R, double* gap, int* nevals_out)
     *gap = mingap;
     *nevals_out = evals;
     free(U); free(Abuf); free(sbest); free(starts); free(wk);
-    return rbest;
+    *rank_out = rbest;
+    if (!L->gused) gbest = rbest >= 0 ? L->cidx[rbest] : -1;
+    return gbest;
 }
 
 /* Predictive equations (Eq. predgp, preds2) on the final design. */
@@ -565,6 +629,45 @@ static void predict(loc_t* L, const double* yS, double* mean, double* s2)
  * order; gap_out[n-n0] the smallest relative gap of the step's decisions;
  * nevals_out[n-n0] the ALC evaluations a ray step made (0 when exhaustive).
  */
+/* Allocates a location's state; the candidates must be filled in. */
+static void loc_init(loc_t* L, const double* X, int64_t N, int p, const double* lo,
+                     const double* hi, const double* x, int n0, int n, int nc, double theta,
+                     double g, int32_t* cidx)
+{
+    L->p = p; L->nc = nc; L->n0 = n0; L->n = n; L->theta = theta; L->g = g;
+    L->x = x; L->lo = lo; L->hi = hi; L->X = X; L->N = N; L->cidx = cidx;
+    L->cx = (double*)malloc(sizeof(double) * (size_t)nc * p);
+    L->S = (double*)malloc(sizeof(double) * (size_t)n * p);
+    L->Kinv = (double*)calloc((size_t)n * n, sizeof(double));
+    L->kx = (double*)malloc(sizeof(double) * (size_t)n);
+    L->work = (double*)malloc(sizeof(double) * (size_t)(4 * n + 4 * p));
+    L->used = (unsigned char*)calloc((size_t)nc, 1);
+    L->sel = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    L->gsel = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    L->gused = g_snap_scope ? (unsigned char*)calloc((size_t)N, 1) : NULL;
+    L->j = 0;
+    lagp_oracle_knn(X, N, p, x, nc, cidx, NULL);
+    for (int r = 0; r < nc; ++r)
+        memcpy(L->cx + (size_t)r * p, X + (int64_t)cidx[r] * p, sizeof(double) * p);
+}
+
+static void loc_free(loc_t* L)
+{
+    free(L->cx); free(L->S); free(L->Kinv); free(L->kx); free(L->work);
+    free(L->used); free(L->sel); free(L->gsel); free(L->gused);
+}
+
+/* One greedy step: the next point by the chosen search, added to the design.
+   Returns 0 or ST_BAD_UPDATE. */
+static int greedy_step(loc_t* L, int search, int nrays, double* gap, int* ne);
+
+/*
+ * Whole path for one location: kNN candidates, n0 nearest start, greedy
+ * selection for j = n0..n-1 (exhaustive: search = 0, ray: search = 1), then
+ * the predictive equations.  sel_out[n] receives design indices in selection
+ * order; gap_out[n-n0] the smallest relative gap of the step's decisions;
+ * nevals_out[n-n0] the ALC evaluations a ray step made (0 when exhaustive).
+ */
 static int one_location(const double* X, const double* Y, int64_t N, int p,
                         const double* lo, const double* hi, const double* x,
                         int n0, int n, int nc, double theta, double g, int search,
@@ -573,21 +676,8 @@ static int one_location(const double* X, const double* Y, int64_t N, int p,
 {
     int32_t* cidx = (int32_t*)malloc(sizeof(int32_t) * (size_t)nc);
     loc_t L;
-    L.p = p; L.nc = nc; L.n0 = n0; L.n = n; L.theta = theta; L.g = g;
-    L.x = x; L.lo = lo; L.hi = hi;
-    L.cx = (double*)malloc(sizeof(double) * (size_t)nc * p);
-    L.S = (double*)malloc(sizeof(double) * (size_t)n * p);
-    L.Kinv = (double*)calloc((size_t)n * n, sizeof(double));
-    L.kx = (double*)malloc(sizeof(double) * (size_t)n);
-    L.work = (double*)malloc(sizeof(double) * (size_t)(4 * n + 4 * p));
-    L.used = (unsigned char*)calloc((size_t)nc, 1);
-    L.sel = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
-    L.j = 0;
+    loc_init(&L, X, N, p, lo, hi, x, n0, n, nc, theta, g, cidx);
     int status = 0;
-
-    lagp_oracle_knn(X, N, p, x, nc, cidx, NULL);
-    for (int r = 0; r < nc; ++r)
-        memcpy(L.cx + (size_t)r * p, X + (int64_t)cidx[r] * p, sizeof(double) * p);
 
     for (int r = 0; r < n0 && !status; ++r)
         if (!(add_point(&L, r) > 0.0)) status |= ST_BAD_UPDATE;
@@ -595,27 +685,39 @@ static int one_location(const double* X, const double* Y, int64_t N, int p,
     for (int j = n0; j < n && !status; ++j) {
         double gap = 0.0;
         int ne = 0;
-        int r = (search == 0) ? search_exhaustive(&L, &gap)
-                              : search_ray(&L, nrays, &gap, &ne);
+        status |= greedy_step(&L, search, nrays, &gap, &ne);
         gap_out[j - n0] = gap;
         nevals_out[j - n0] = ne;
-        if (r < 0 || !(add_point(&L, r) > 0.0)) status |= ST_BAD_UPDATE;
     }
 
     if (!status) {
         double* yS = (double*)malloc(sizeof(double) * (size_t)n);
-        for (int i = 0; i < n; ++i) yS[i] = Y[cidx[L.sel[i]]];
+        for (int i = 0; i < n; ++i) yS[i] = Y[L.gsel[i]];
         predict(&L, yS, mean, s2);
         free(yS);
-        for (int i = 0; i < n; ++i) sel_out[i] = cidx[L.sel[i]];
+        for (int i = 0; i < n; ++i) sel_out[i] = L.gsel[i];
     } else {
         *mean = NAN;
         *s2 = NAN;
-        for (int i = 0; i < n; ++i) sel_out[i] = (i < L.j) ? cidx[L.sel[i]] : -1;
+        for (int i = 0; i < n; ++i) sel_out[i] = (i < L.j) ? L.gsel[i] : -1;
     }
-    free(cidx); free(L.cx); free(L.S); free(L.Kinv); free(L.kx); free(L.work);
-    free(L.used); free(L.sel);
+    free(cidx);
+    loc_free(&L);
     return status;
+}
+
+static int greedy_step(loc_t* L, int search, int nrays, double* gap, int* ne)
+{
+    int r = -1;
+    int64_t gi = -1;
+    if (search == 0) {
+        r = search_exhaustive(L, gap);
+        gi = r >= 0 ? L->cidx[r] : -1;
+    } else {
+        gi = search_ray(L, nrays, gap, ne, &r);
+    }
+    if (gi < 0 || !(add_point_g(L, gi, r) > 0.0)) return ST_BAD_UPDATE;
+    return 0;
 }
 
 /* Bounding box of the design, per dimension. */
@@ -870,6 +972,8 @@ double lagp_oracle_mle_theta(const double* S, const double* y, int n, int p, dou
 static void reset_location(loc_t* L, double theta)
 {
     L->theta = theta;
+    if (L->gused)
+        for (int i = 0; i < L->j; ++i) L->gused[L->gsel[i]] = 0;
     L->j = 0;
     memset(L->used, 0, (size_t)L->nc);
     for (int i = 0; i < L->n * L->n; ++i) L->Kinv[i] = 0.0;
@@ -883,8 +987,7 @@ static int build_design(loc_t* L, int search, int nrays)
     for (int j = L->n0; j < L->n; ++j) {
         double gap = 0.0;
         int ne = 0;
-        int r = (search == 0) ? search_exhaustive(L, &gap) : search_ray(L, nrays, &gap, &ne);
-        if (r < 0 || !(add_point(L, r) > 0.0)) return ST_BAD_UPDATE;
+        if (greedy_step(L, search, nrays, &gap, &ne)) return ST_BAD_UPDATE;
     }
     return 0;
 }
@@ -903,49 +1006,39 @@ static int one_location_mle(const double* X, const double* Y, int64_t N, int p,
 {
     int32_t* cidx = (int32_t*)malloc(sizeof(int32_t) * (size_t)nc);
     loc_t L;
-    L.p = p; L.nc = nc; L.n0 = n0; L.n = n; L.g = g;
-    L.x = x; L.lo = lo; L.hi = hi;
-    L.cx = (double*)malloc(sizeof(double) * (size_t)nc * p);
-    L.S = (double*)malloc(sizeof(double) * (size_t)n * p);
-    L.Kinv = (double*)calloc((size_t)n * n, sizeof(double));
-    L.kx = (double*)malloc(sizeof(double) * (size_t)n);
-    L.work = (double*)malloc(sizeof(double) * (size_t)(4 * n + 4 * p));
-    L.used = (unsigned char*)calloc((size_t)nc, 1);
-    L.sel = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    loc_init(&L, X, N, p, lo, hi, x, n0, n, nc, theta0, g, cidx);
     int32_t* order = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t* orank = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
     double* yS = (double*)malloc(sizeof(double) * (size_t)n);
     int status = 0;
-
-    lagp_oracle_knn(X, N, p, x, nc, cidx, NULL);
-    for (int r = 0; r < nc; ++r)
-        memcpy(L.cx + (size_t)r * p, X + (int64_t)cidx[r] * p, sizeof(double) * p);
 
     double theta = theta0;
     for (int s = 0; s < stages && !status; ++s) {
         reset_location(&L, theta);
         status = build_design(&L, search, nrays);
         if (status) break;
-        for (int i = 0; i < n; ++i) yS[i] = Y[cidx[L.sel[i]]];
+        for (int i = 0; i < n; ++i) yS[i] = Y[L.gsel[i]];
         theta = lagp_oracle_mle_theta(L.S, yS, n, p, theta, g, tmin, tmax, 1e-10, 200, NULL);
     }
     if (!status) {
-        memcpy(order, L.sel, sizeof(int32_t) * (size_t)n);
+        memcpy(order, L.gsel, sizeof(int32_t) * (size_t)n);
+        memcpy(orank, L.sel, sizeof(int32_t) * (size_t)n);
         reset_location(&L, theta);
         for (int i = 0; i < n && !status; ++i)
-            if (!(add_point(&L, order[i]) > 0.0)) status = ST_BAD_UPDATE;
+            if (!(add_point_g(&L, order[i], orank[i]) > 0.0)) status = ST_BAD_UPDATE;
     }
     if (!status) {
         predict(&L, yS, mean, s2);
         *theta_out = theta;
-        for (int i = 0; i < n; ++i) sel_out[i] = cidx[L.sel[i]];
+        for (int i = 0; i < n; ++i) sel_out[i] = L.gsel[i];
     } else {
         *mean = NAN;
         *s2 = NAN;
         *theta_out = NAN;
         for (int i = 0; i < n; ++i) sel_out[i] = -1;
     }
-    free(cidx); free(L.cx); free(L.S); free(L.Kinv); free(L.kx); free(L.work);
-    free(L.used); free(L.sel); free(order); free(yS);
+    free(cidx); free(order); free(orank); free(yS);
+    loc_free(&L);
     return status;
 }
 

@@ -173,13 +173,13 @@ struct KtSmem {
                                                                    : 120 * 1024;
 };
 
-template <int KA>
+template <int KA, bool SPLIT>
 __global__ void __launch_bounds__(KT_THREADS, 1)
 knn_tc(const float* __restrict__ Btiles, int64_t ntiles, int p, const double* __restrict__ xref,
        int64_t M, const double* __restrict__ center, const unsigned* __restrict__ maxn2_bits,
        int nc_max, const int32_t* __restrict__ nc_loc, int cap, const float* __restrict__ pilot,
        KnnEntry* __restrict__ buf, int32_t* __restrict__ cnt_out, int32_t* __restrict__ seg_out,
-       unsigned* __restrict__ status, int split) {
+       unsigned* __restrict__ status) {
   using L = KtSmem<KA>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
@@ -356,7 +356,7 @@ knn_tc(const float* __restrict__ Btiles, int64_t ntiles, int p, const double* __
             KnnEntry e;
             e.d = fmaxf(d, 0.f);
             e.idx = pbase + c0 + u;
-            if (split) {
+            if (SPLIT) {
               // segments of one location share its buffer through a counter
               const int slot = atomicAdd(&seg_out[q * KT_GROUPS], 1);
               if (slot < cap) buf[q * (int64_t)cap + slot] = e;
@@ -372,7 +372,7 @@ knn_tc(const float* __restrict__ Btiles, int64_t ntiles, int p, const double* __
     cnt_sm[g * KT_M + c] = mycnt;
     atomicAdd(&below_sm[c], mybelow);
     kt_epi_barrier();
-    if (split) {
+    if (SPLIT) {
       // the location's totals come together in knn_tc_join once every
       // segment is done
       if (g == 0 && q < M && below_sm[c] > 0) atomicAdd(&seg_out[q * KT_GROUPS + 1], below_sm[c]);
@@ -499,12 +499,13 @@ cudaError_t launch_knn_tc(int64_t Npad, int p, const double* xref, int64_t M, in
 #define KT_CASE(V)                                                                              \
   case V: {                                                                                     \
     const size_t sm = KtSmem<V>::BYTES;                                                         \
-    err = cudaFuncSetAttribute(knn_tc<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+    auto kern = split ? knn_tc<V, true> : knn_tc<V, false>;                                     \
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);     \
     if (err != cudaSuccess) return err;                                                         \
     prof_begin("knn_tc", s);                                                                    \
-    knn_tc<V><<<g3, KT_THREADS, sm, s>>>(ws.Btc, ntiles, p, xref, M, ws.center, ws.maxn2,       \
-                                         nc_max, nc_loc, cap, ws.knn_thr, kbuf, ws.knn_cnt,     \
-                                         ws.knn_seg, ws.status, split);                         \
+    kern<<<g3, KT_THREADS, sm, s>>>(ws.Btc, ntiles, p, xref, M, ws.center, ws.maxn2, nc_max,    \
+                                    nc_loc, cap, ws.knn_thr, kbuf, ws.knn_cnt, ws.knn_seg,      \
+                                    ws.status);                                                 \
     prof_end(s);                                                                                \
     break;                                                                                      \
   }

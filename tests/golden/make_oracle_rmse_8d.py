@@ -7,8 +7,12 @@ the 1% bar is checked without sampling noise.
 
 Calls only the oracle (and the seeded input generator).  The oracle is plain
 binary64 C without contraction, so the values do not depend on the host.
-Takes hours on a few cores:  python tests/golden/make_oracle_rmse_8d.py [threads]
+Takes hours on a few cores:
+    python tests/golden/make_oracle_rmse_8d.py [--threads T] [--search ray|exhaustive]
+                                               [--out PATH]
+With --search, only that search's line of the output file is (re)written.
 """
+import argparse
 import os
 import sys
 
@@ -24,22 +28,38 @@ from paper_1409_0074_gb300 import workloads as W  # noqa: E402
 OUT = os.path.join(HERE, "oracle_rmse_sinusoid8d.txt")
 
 
+HEADER = ["# FP64 oracle over all 100,000 locations of the 8-d workload",
+          "# (python tests/golden/make_oracle_rmse_8d.py); search rmse locations status_bad"]
+
+
+def oracle_rmse(w, search, threads):
+    err2, bad = 0.0, 0
+    for c0 in range(0, w.M, 2000):
+        r = oracle.predict(w.X, w.Y, w.Xref[c0:c0 + 2000], w.n0, w.n, w.nc, w.theta, w.g,
+                           search, nrays=8, nthreads=threads)
+        err2 += float(np.sum((r["mean"] - w.Ytrue[c0:c0 + 2000]) ** 2))
+        bad += int(np.sum(r["status"] != 0))
+        print(search, c0 + 2000, flush=True)
+    return "%s %.17g %d %d" % (search, np.sqrt(err2 / w.M), w.M, bad)
+
+
 def main():
-    threads = int(sys.argv[1]) if len(sys.argv) > 1 else 0
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--search", choices=["ray", "exhaustive"], default=None)
+    ap.add_argument("--out", default=OUT)
+    a = ap.parse_args()
     w = W.large_8d(M=100_000)
-    lines = ["# FP64 oracle over all 100,000 locations of the 8-d workload",
-             "# (python tests/golden/make_oracle_rmse_8d.py); search rmse locations status_bad"]
-    for search in ("ray", "exhaustive"):
-        err2, bad = 0.0, 0
-        for c0 in range(0, w.M, 2000):
-            r = oracle.predict(w.X, w.Y, w.Xref[c0:c0 + 2000], w.n0, w.n, w.nc, w.theta, w.g,
-                               search, nrays=8, nthreads=threads)
-            err2 += float(np.sum((r["mean"] - w.Ytrue[c0:c0 + 2000]) ** 2))
-            bad += int(np.sum(r["status"] != 0))
-            print(search, c0 + 2000, flush=True)
-        lines.append("%s %.17g %d %d" % (search, np.sqrt(err2 / w.M), w.M, bad))
-    with open(OUT, "w") as fh:
-        fh.write("\n".join(lines) + "\n")
+    rows = {}
+    if os.path.exists(a.out):
+        for line in open(a.out):
+            if line.strip() and not line.startswith("#"):
+                rows[line.split()[0]] = line.strip()
+    for search in ([a.search] if a.search else ["ray", "exhaustive"]):
+        rows[search] = oracle_rmse(w, search, a.threads)
+        with open(a.out, "w") as fh:
+            fh.write("\n".join(HEADER + [rows[k] for k in ("ray", "exhaustive") if k in rows])
+                     + "\n")
 
 
 if __name__ == "__main__":
