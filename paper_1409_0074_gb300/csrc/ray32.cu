@@ -55,8 +55,7 @@ struct RayParams {
   int32_t* selected;
   double* tie_gap;
   int32_t* nevals;
-  double* g64;          // per warp slot: packed L^{-1} (n(n+1)/2), kx, z, zy, kvec, l (n each),
-                        // then 128 doubles of records for the balanced sums
+  double* g64;          // per warp slot: packed L^{-1} (n(n+1)/2) then kx, z, zy, kvec, l (n each)
   int64_t g64_stride;
   unsigned* status;
   unsigned* queue;      // work counter (zero at launch)
@@ -165,125 +164,6 @@ __device__ __forceinline__ double warp_sum64(double v) {
   return v;
 }
 
-// ---- balanced FP64 sums over a packed lower triangle ----
-// The T = j (j + 1) / 2 products of a triangular product are split into 32
-// equal contiguous ranges, one per lane, so that every lane runs the same
-// number of FP64 instructions (a whole-row split would leave the warp waiting
-// for its longest row).  A segment (row or column) that crosses lanes is summed
-// by its first lane from the partials of the following lanes in lane order,
-// so the result does not depend on timing.  rec: 4 x 32 doubles of scratch.
-struct TriRec {
-  int first_seg, last_seg;     // continued segment at the start (-2: empty range) /
-  double first_val, last_val;  // continuing one at the end (-1: none)
-};
-
-// Segment of flattened element e when segment s holds len(s) elements and
-// starts at start(s) (both increasing): the largest s with start(s) <= e.
-__device__ __forceinline__ int tri_row_of(int e) {          // start(s) = tri(s)
-  int s = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
-  while (tri(s + 1) <= e) ++s;
-  while (tri(s) > e) --s;
-  return s;
-}
-__device__ __forceinline__ int col_start(int k, int j) { return k * j - k * (k - 1) / 2; }
-__device__ __forceinline__ int tri_col_of(int f, int j) {   // start(k) = k j - k (k - 1) / 2
-  const float b = 2.f * (float)j + 1.f;
-  int k = (int)((b - sqrtf(fmaxf(b * b - 8.f * (float)f, 0.f))) * 0.5f);
-  if (k < 0) k = 0;
-  while (k + 1 < j && col_start(k + 1, j) <= f) ++k;
-  while (k > 0 && col_start(k, j) > f) --k;
-  return k;
-}
-
-// Publishes a lane's records, then lets each segment's first lane finish it.
-// out(seg, value) receives every segment's complete sum exactly once.
-template <typename Out>
-__device__ __forceinline__ void tri_finish(const TriRec& r, double* rec, Out out) {
-  const int lane = threadIdx.x & 31;
-  rec[lane] = (double)r.first_seg;
-  rec[32 + lane] = r.first_val;
-  __syncwarp();
-  if (r.last_seg >= 0) {
-    double acc = r.last_val;
-    for (int l2 = lane + 1; l2 < 32; ++l2) {
-      const int f = (int)rec[l2];
-      if (f == -2) continue;               // an empty range: the segment goes on past it
-      if (f != r.last_seg) break;
-      acc += rec[32 + l2];
-    }
-    out(r.last_seg, acc);
-  }
-  __syncwarp();
-}
-
-// l[i] = sum_{k <= i} L[i][k] x[k], i < j (L packed by rows: L[i][k] = Lg[tri(i) + k])
-template <typename Out>
-__device__ __forceinline__ void tri_rows64(const double* Lg, const double* x, int j, double* rec,
-                                           Out out) {
-  const int lane = threadIdx.x & 31;
-  const int T = tri(j);
-  const int e0 = (lane * T) >> 5, e1 = ((lane + 1) * T) >> 5;
-  TriRec r{e0 < e1 ? -1 : -2, -1, 0.0, 0.0};
-  if (e0 < e1) {
-    int i = tri_row_of(e0), k = e0 - tri(i);
-    const bool cont = k > 0;          // the first row began in an earlier lane
-    bool first = true;
-    double acc = 0.0;
-    for (int e = e0; e < e1; ++e) {
-      acc = fma(Lg[e], x[k], acc);
-      if (++k > i) {                  // row i ends here
-        if (first && cont) { r.first_seg = i; r.first_val = acc; }
-        else out(i, acc);
-        first = false;
-        acc = 0.0;
-        ++i;
-        k = 0;
-      }
-    }
-    if (k > 0) {                      // row i goes on in the next lane
-      if (first && cont) { r.first_seg = i; r.first_val = acc; }
-      else { r.last_seg = i; r.last_val = acc; }
-    }
-  }
-  tri_finish(r, rec, out);
-}
-
-// c[k] = sum_{i = k}^{j-1} l[i] L[i][k], k < j (column sums of the packed rows)
-template <typename Out>
-__device__ __forceinline__ void tri_cols64(const double* Lg, const double* l, int j, double* rec,
-                                           Out out) {
-  const int lane = threadIdx.x & 31;
-  const int T = tri(j);
-  const int f0 = (lane * T) >> 5, f1 = ((lane + 1) * T) >> 5;
-  TriRec r{f0 < f1 ? -1 : -2, -1, 0.0, 0.0};
-  if (f0 < f1) {
-    int k = tri_col_of(f0, j), i = k + (f0 - col_start(k, j));
-    const bool cont = i > k;          // the first column began in an earlier lane
-    bool first = true;
-    double acc = 0.0;
-    int idx = tri(i) + k;
-    for (int f = f0; f < f1; ++f) {
-      acc = fma(l[i], Lg[idx], acc);
-      ++i;
-      idx += i;                        // tri(i + 1) + k = tri(i) + k + i + 1
-      if (i == j) {                    // column k ends here
-        if (first && cont) { r.first_seg = k; r.first_val = acc; }
-        else out(k, acc);
-        first = false;
-        acc = 0.0;
-        ++k;
-        i = k;
-        idx = tri(i) + k;
-      }
-    }
-    if (i > k && i < j) {             // column k goes on in the next lane
-      if (first && cont) { r.first_seg = k; r.first_val = acc; }
-      else { r.last_seg = k; r.last_val = acc; }
-    }
-  }
-  tri_finish(r, rec, out);
-}
-
 enum { PH_ALC0 = 0, PH_FIRST = 1, PH_ITER = 2, PH_DONE = 3 };
 
 // One location, by one warp, in the warp's shared-memory region and FP64 slot.
@@ -318,7 +198,6 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
   double* zy64 = z64 + ldn;
   double* kv64 = zy64 + ldn;
   double* l64 = kv64 + ldn;
-  double* rec64 = l64 + ldn;          // 4 x 32 doubles: the balanced sums' records
   const double* xq = P.xref + loc * p;
 
   const double theta = P.theta_loc ? P.theta_loc[loc] : P.theta;
@@ -356,10 +235,9 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
     // instruction costs the same whatever its active lanes, so every lane
     // evaluates the scalar tail.
     double vv = 0.0, lz = 0.0, lzy = 0.0;
-    tri_rows64(Lg, kv64, j, rec64, [&](int i, double acc) { l64[i] = acc; });
-    __syncwarp();
     for (int i = lane; i < j; i += 32) {
-      const double acc = l64[i];
+      const double acc = dot64_ilp(Lg + tri(i), kv64, i + 1);
+      l64[i] = acc;
       vv = fma(acc, acc, vv);
       lz = fma(acc, z64[i], lz);
       lzy = fma(acc, zy64[i], lzy);
@@ -373,11 +251,18 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
     const double inv_d = rsqrt(v);
     double* Lj = Lg + tri(j);
     float* Lfj = Lf + roff(j);
-    tri_cols64(Lg, l64, j, rec64 + 64, [&](int k, double acc) {
-      const double rk = -acc * inv_d;
+    for (int k = lane; k < j; k += 32) {
+      double a0 = 0.0, a1 = 0.0;
+      int i = k;
+      for (; i + 1 < j; i += 2) {
+        a0 = fma(l64[i], Lg[tri(i) + k], a0);
+        a1 = fma(l64[i + 1], Lg[tri(i + 1) + k], a1);
+      }
+      if (i < j) a0 = fma(l64[i], Lg[tri(i) + k], a0);
+      const double rk = -(a0 + a1) * inv_d;
       Lj[k] = rk;
       Lfj[k] = (float)rk;
-    });
+    }
     if (lane == 0) {
       Lj[j] = inv_d;
       Lfj[j] = (float)inv_d;
@@ -666,7 +551,7 @@ __global__ void __launch_bounds__(RW * 32, 20 / RW) ray32_kernel(RayParams P) {
   }
 }
 
-size_t ray32_g64_doubles(int n_max) { return (size_t)tri(n_max) + 5 * (size_t)n_max + 128; }
+size_t ray32_g64_doubles(int n_max) { return (size_t)tri(n_max) + 5 * (size_t)n_max; }
 
 // Warp slots for a chunk: at least one CTA of the widest choice (4 warps) and a
 // multiple of 4, so that every warp of every launched CTA owns a slot.
