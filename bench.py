@@ -440,7 +440,8 @@ def run_extra(args, w, tensors, search, precision, M, steps=2):
     ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
     mean = torch.empty(M, dtype=torch.float64, device="cuda")
     s2 = torch.empty(M, dtype=torch.float64, device="cuda")
-    nev = torch.zeros((M, w.n), dtype=torch.int32, device="cuda") if search == "ray" else None
+    nev = (torch.zeros((M, w.n), dtype=torch.int32, device="cuda") if search.startswith("ray")
+           else None)
     go = lambda: lagp.laGP_build_and_predict(X, Y, Xr, w.n0, w.n, w.nc, w.theta, w.g, s,
                                              w.nrays, pr, mean, s2, ws, nevals=nev)
     go()
@@ -822,6 +823,9 @@ def main():
             ex["exhaustive_fp32_tc"] = run_extra(args, w, r["tensors"], "exhaustive", "fp32_tc",
                                                  w.M)
             ex["ray_fp64"] = run_extra(args, w, r["tensors"], "ray", "fp64", min(w.M, 4000))
+            ex["ray_full_scope_fp32"] = run_extra(args, w, r["tensors"], "ray_full", "fp32", w.M)
+            ex["ray_full_scope_fp64"] = run_extra(args, w, r["tensors"], "ray_full", "fp64",
+                                                  min(w.M, 4000))
             ex["exhaustive_fp64"] = run_extra(args, w, r["tensors"], "exhaustive", "fp64",
                                               min(w.M, 1000), steps=1)
             line["other_forms"] = ex

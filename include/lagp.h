@@ -43,9 +43,16 @@
 extern "C" {
 #endif
 
-/* Search for the next design point (Sec 2.2 exhaustive, Sec 4 rays). */
+/* Search for the next design point (Sec 2.2 exhaustive, Sec 4 rays).
+ * LAGP_RAY snaps a ray step's best point to the nearest unselected candidate
+ * (the N_close nearest design points).  LAGP_RAY_FULL snaps it to the nearest
+ * point of the whole design X_N outside the local design (Sec 5 places no N'
+ * limit on ray searches), through a k-d tree over X_N built with the design's
+ * preparation; ray starts still come from the candidates, and ties go to the
+ * point nearer x, then to the lower design index. */
 #define LAGP_EXHAUSTIVE 0
 #define LAGP_RAY 1
+#define LAGP_RAY_FULL 2
 
 /* Arithmetic of the greedy loop.
  * LAGP_FP64: every step in binary64 with the paper's explicit K_j^{-1} and
@@ -100,8 +107,8 @@ size_t laGP_workspace_bytes(int64_t N, int p, int64_t M, int n, int N_close, int
  *   N_close   candidates per location (n <= N_close <= min(N, 4096))
  *   theta     lengthscale (> 0)
  *   g         nugget (>= 0)
- *   search    LAGP_EXHAUSTIVE or LAGP_RAY
- *   nrays     rays per step for LAGP_RAY (<= 0 selects p; at most 16 and at
+ *   search    LAGP_EXHAUSTIVE, LAGP_RAY or LAGP_RAY_FULL
+ *   nrays     rays per step of a ray search (<= 0 selects p; at most 16 and at
  *             most N_close - n); ignored for LAGP_EXHAUSTIVE
  *   precision LAGP_FP64, LAGP_FP32_SCORE or LAGP_FP32_SCORE_TC
  *   n_loc     device [M] int32 or NULL: per-location final size (each in
@@ -114,6 +121,8 @@ size_t laGP_workspace_bytes(int64_t N, int p, int64_t M, int n, int N_close, int
  *             the predictive variance is s2 * n / (n - 2)
  *   selected  device [M][n] int32 out or NULL: design indices in selection
  *             order (the n0 nearest first); entries past a location's n are -1
+ *             (with LAGP_RAY_FULL a design may hold points outside the
+ *             candidates)
  *   tie_gap   device [M][n] out or NULL: entry j - n0 holds the smallest
  *             relative gap among the comparisons that decided step j (argmax
  *             of ALC; for rays also Brent's comparisons, the s = 0 check and

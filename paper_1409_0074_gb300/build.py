@@ -30,6 +30,7 @@ UNITS = {
     "schedule.cu": [],
     "serve.cu": [],
     "mle.cu": [],
+    "kdtree.cu": [],
 }
 
 

@@ -16,8 +16,10 @@
 // rows K(S_i, c_r) in a global cache laid out [i][r] so that consecutive
 // threads (candidates) read consecutive addresses.
 #include <cstdint>
+#include <cstring>
 
 #include "common.cuh"
+#include "kdtree.cuh"
 #include "lagp_internal.h"
 
 namespace lagp {
@@ -50,6 +52,8 @@ struct D64Params {
   int32_t* nevals;
   double* Kc;          // exhaustive correlation cache [M][n_max][nc_max]
   unsigned* status;
+  int full;            // ray snaps over all of X_N through the k-d tree
+  KdView<double> kd;   // the tree in binary64 (full scope)
 };
 
 // ----- exact top-2 reductions ------------------------------------------------
@@ -118,7 +122,9 @@ struct Loc {
   double* xs;        // [p]
   double* scal;      // [4] broadcast scalars
   Top2* red;         // [WARPS]
-  int* sel;          // [n_max] selected ranks
+  int* sel;          // [n_max] selected ranks (-1: not a candidate)
+  int* gsel;         // [n_max] selected design indices
+  int* stk;          // [KD_STACK] k-d tree walk (full scope)
   int* rnev;         // [R]
   int* starts;       // [R]
   int* iscal;        // [4]
@@ -133,10 +139,10 @@ __device__ __forceinline__ const double* cand_coords(const D64Params& P, const i
 
 // Adds candidate rank r (partitioned-inverse step).  Returns false when v <= 0.
 template <int SEARCH>
-__device__ bool add_point(const D64Params& P, Loc& L, const int32_t* cl, int nc, int r,
+__device__ bool add_point(const D64Params& P, Loc& L, const int32_t* cl, int nc, int gi, int r,
                           double* Kc_loc) {
   const int tid = threadIdx.x, p = P.p, j = L.j, ld = P.n_max;
-  const double* c = cand_coords(P, cl, r);
+  const double* c = P.X + (int64_t)gi * p;
   if (tid < p) L.S[j * p + tid] = c[tid];
   __syncthreads();
   for (int i = tid; i < j; i += blockDim.x) L.kvec[i] = corr64(L.S + i * p, L.S + j * p, p, L.theta);
@@ -170,7 +176,8 @@ __device__ bool add_point(const D64Params& P, Loc& L, const int32_t* cl, int nc,
     L.Kinv[j * ld + j] = __ddiv_rn(1.0, v);
     L.kx[j] = corr64(L.S + j * p, L.xq, p, L.theta);
     L.sel[j] = r;
-    L.used[r] = 1;
+    L.gsel[j] = gi;
+    if (r >= 0) L.used[r] = 1;
   }
   if (SEARCH == SEARCH_EXHAUSTIVE) {
     double* row = Kc_loc + (int64_t)j * P.nc_max;
@@ -325,8 +332,9 @@ __device__ double brent_ray(const D64Params& P, Loc& L, const double* A, const d
   return fx;
 }
 
+// Returns the chosen design index; *rank_out its candidate rank (-1: none).
 __device__ int search_ray(const D64Params& P, Loc& L, const int32_t* cl, int nc, double* gap_out,
-                          int* nev_out) {
+                          int* nev_out, int* rank_out) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int p = P.p, R = P.R, j = L.j;
   const double inf = __longlong_as_double(0x7ff0000000000000ll);
@@ -406,6 +414,44 @@ __device__ int search_ray(const D64Params& P, Loc& L, const int32_t* cl, int nc,
     L.iscal[0] = ev;
   }
   __syncthreads();
+  if (P.full) {
+    // snap over all of X_N outside the design (warp 0 walks the k-d tree); the
+    // step's starts are forbidden unless they equal x*; ties to the point
+    // nearer x, then to the lower design index
+    if (warp == 0) {
+      const KdView<double>& V = P.kd;
+      auto excluded = [&](int32_t gi, int64_t, bool allow_starts) -> bool {
+        for (int i = 0; i < j; ++i) if (L.gsel[i] == gi) return true;
+        if (allow_starts) return false;
+        const double* c = P.X + (int64_t)gi * p;
+        for (int t = 0; t < R; ++t) {
+          if (cl[L.starts[t]] != gi) continue;
+          for (int k = 0; k < p; ++k) if (c[k] != L.xs[k]) return true;
+        }
+        return false;
+      };
+      auto dist = [&](int64_t, int32_t gi) { return sqdist64(P.X + (int64_t)gi * p, L.xs, p); };
+      auto distx = [&](int64_t, int32_t gi) { return sqdist64(P.X + (int64_t)gi * p, L.xq, p); };
+      const KdTop<double> b = kd_nearest<double>(V, L.xs, 1e-12, L.stk, excluded, dist, distx);
+      if (lane == 0) {
+        L.iscal[1] = b.i1;
+        L.iscal[2] = 0x7fffffff;
+        double mg = L.scal[1];
+        if (b.d2 < inf) mg = fmin(mg, relgap64(b.d1, b.d2));
+        L.scal[2] = mg;
+      }
+    }
+    __syncthreads();
+    const int gi = L.iscal[1];
+    for (int r = tid; r < nc; r += blockDim.x)
+      if (cl[r] == gi) atomicMin(&L.iscal[2], r);
+    __syncthreads();
+    *rank_out = L.iscal[2] != 0x7fffffff ? L.iscal[2] : -1;
+    *gap_out = L.scal[2];
+    *nev_out = L.iscal[0];
+    __syncthreads();
+    return gi;
+  }
   // snap: nearest allowed unselected candidate, ties to the lower rank
   Top2 t;
   t.b1 = inf; t.b2 = inf; t.i1 = -1;
@@ -439,7 +485,8 @@ __device__ int search_ray(const D64Params& P, Loc& L, const int32_t* cl, int nc,
   if (b.b2 < inf) mg = fmin(mg, relgap64(b.b1, b.b2));
   *gap_out = mg;
   *nev_out = L.iscal[0];
-  return b.i1;
+  *rank_out = b.i1;
+  return b.i1 >= 0 ? cl[b.i1] : -1;
 }
 
 // ----- predictive equations (Eq. predgp, preds2) -------------------------------
@@ -448,7 +495,7 @@ __device__ void predict(const D64Params& P, Loc& L, const int32_t* cl, double* m
   double* yS = L.rkz;        // reuse ray buffers: [n] each
   double* ky = L.ru;
   double* kk = L.rkz + ld;
-  for (int i = tid; i < n; i += blockDim.x) yS[i] = P.Y[cl[L.sel[i]]];
+  for (int i = tid; i < n; i += blockDim.x) yS[i] = P.Y[L.gsel[i]];
   __syncthreads();
   for (int i = tid; i < n; i += blockDim.x) {
     const double* Ki = L.Kinv + i * ld;
@@ -512,6 +559,8 @@ __global__ void __launch_bounds__(D64_THREADS) design64(D64Params P) {
   L.red = reinterpret_cast<Top2*>(dp); dp += 3 * D64_WARPS;
   int* ip = reinterpret_cast<int*>(dp);
   L.sel = ip; ip += ld;
+  L.gsel = ip; ip += ld;
+  L.stk = ip; ip += KD_STACK;
   L.rnev = ip; ip += R;
   L.starts = ip; ip += R;
   L.iscal = ip; ip += 4;
@@ -533,18 +582,22 @@ __global__ void __launch_bounds__(D64_THREADS) design64(D64Params P) {
   __syncthreads();
 
   bool ok = (n >= P.n0) && (n <= nc) && (n <= ld);
-  for (int r = 0; r < P.n0 && ok; ++r) ok = add_point<SEARCH>(P, L, cl, nc, r, Kc_loc);
+  for (int r = 0; r < P.n0 && ok; ++r) ok = add_point<SEARCH>(P, L, cl, nc, cl[r], r, Kc_loc);
   for (int j = P.n0; j < n && ok; ++j) {
     double gap = 0.0;
     int ne = 0;
-    int r;
-    if (SEARCH == SEARCH_EXHAUSTIVE) r = search_exhaustive(P, L, cl, nc, Kc_loc, &gap);
-    else r = search_ray(P, L, cl, nc, &gap, &ne);
+    int r, gi;
+    if (SEARCH == SEARCH_EXHAUSTIVE) {
+      r = search_exhaustive(P, L, cl, nc, Kc_loc, &gap);
+      gi = r >= 0 ? cl[r] : -1;
+    } else {
+      gi = search_ray(P, L, cl, nc, &gap, &ne, &r);
+    }
     if (tid == 0) {
       if (P.tie_gap) P.tie_gap[loc * ld + (j - P.n0)] = gap;
       if (P.nevals) P.nevals[loc * ld + (j - P.n0)] = ne;
     }
-    ok = (r >= 0) && add_point<SEARCH>(P, L, cl, nc, r, Kc_loc);
+    ok = (gi >= 0) && add_point<SEARCH>(P, L, cl, nc, gi, r, Kc_loc);
   }
   if (ok) {
     predict(P, L, cl, P.mean + loc, P.s2 + loc);
@@ -555,14 +608,14 @@ __global__ void __launch_bounds__(D64_THREADS) design64(D64Params P) {
   }
   if (P.selected)
     for (int i = tid; i < ld; i += blockDim.x)
-      P.selected[loc * ld + i] = (i < L.j) ? cl[L.sel[i]] : -1;
+      P.selected[loc * ld + i] = (i < L.j) ? L.gsel[i] : -1;
 }
 
 static size_t smem_design64(int n_max, int p, int nc_max, int R) {
   size_t d = (size_t)n_max * n_max + (size_t)n_max * p + 3 * n_max + 3 * p +
              2 * D64_WARPS * n_max + D64_WARPS * p + 2 * R * p + 3 * R + p + 4 +
              3 * D64_WARPS * ((sizeof(Top2) + 7) / 8);
-  size_t i = (size_t)n_max + 2 * R + 4;
+  size_t i = 2 * (size_t)n_max + KD_STACK + 2 * R + 4;
   return d * 8 + i * 4 + nc_max + 16;
 }
 
@@ -573,6 +626,14 @@ cudaError_t launch_design_fp64(const DesignArgs& a, int search, cudaStream_t s) 
   P.theta = a.theta; P.theta_loc = a.theta_loc; P.g = a.g; P.R = a.nrays; P.lo = a.ws->lo; P.hi = a.ws->hi;
   P.mean = a.mean; P.s2 = a.s2; P.selected = a.selected; P.tie_gap = a.tie_gap;
   P.nevals = a.nevals; P.Kc = a.ws->state64; P.status = a.ws->status;
+  P.full = a.full_scope;
+  if (P.full) {
+    const KdTree& t = a.ws->kd;
+    P.kd.box = t.box64; P.kd.stride = a.p; P.kd.p = a.p; P.kd.D = t.D; P.kd.N = a.N;
+    P.kd.perm = t.perm; P.kd.pts = a.X; P.kd.by_design = true;
+  } else {
+    std::memset(&P.kd, 0, sizeof(P.kd));
+  }
   size_t sm = smem_design64(a.n_max, a.p, a.nc_max, a.nrays);
   cudaError_t err;
   if (search == SEARCH_EXHAUSTIVE) {

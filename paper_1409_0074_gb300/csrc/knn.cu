@@ -503,7 +503,9 @@ cudaError_t launch_prepare(const double* X, int64_t N, int p, int PP, int64_t Np
   prof_end(s);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  return launch_design_to_tc(N, p, PP, Npad, ws, s);
+  if ((err = launch_design_to_tc(N, p, PP, Npad, ws, s)) != cudaSuccess) return err;
+  // the k-d tree of the unlimited ray scope, when the workspace has one
+  return ws.kd.perm ? launch_kd_build(X, ws.Xf, N, p, PP, ws.kd, s) : cudaSuccess;
 }
 
 cudaError_t launch_knn(const double* X, int64_t N, int p, int PP, int64_t Npad,

@@ -49,7 +49,7 @@ size_t layout_request(const Shape& sh, void* base, Workspace* ws) {
   size_t s64 = 0, s32 = 0;
   if (sh.precision == LAGP_FP64) {
     if (sh.search == LAGP_EXHAUSTIVE) s64 = sizeof(double) * ch * sh.n_max * sh.nc_max;
-  } else if (sh.search == LAGP_RAY) {
+  } else if (sh.search != LAGP_EXHAUSTIVE) {
     s64 = sizeof(double) * ray32_slots(ch) * ray32_g64_doubles(sh.n_max);
   } else {
     const size_t slots = exh_slots(ch);
@@ -88,6 +88,11 @@ size_t layout_design(const Shape& sh, void* base, Workspace* ws) {
   w->Xf = static_cast<float*>(c.take(sizeof(float) * sh.Npad * sh.PP));
   w->nx = static_cast<float*>(c.take(sizeof(float) * sh.Npad));
   w->Btc = static_cast<float*>(c.take(sizeof(float) * knn_tc_tile_floats(sh.Npad, sh.p)));
+  if (sh.search == LAGP_RAY_FULL) {
+    kd_carve(sh.N, sh.p, sh.PP, static_cast<char*>(c.take(kd_bytes(sh.N, sh.p, sh.PP))), &w->kd);
+  } else {
+    std::memset(&w->kd, 0, sizeof(w->kd));
+  }
   return c.off;
 }
 
@@ -105,12 +110,13 @@ bool make_shape(int64_t N, int p, int64_t M, int n0, int n, int N_close, int nra
   if (p < 1 || p > LAGP_MAX_P || N < 1 || M < 0) return false;
   if (n0 < 1 || n0 > n || n > LAGP_MAX_N || n > N_close || N_close > N || N_close > 4096)
     return false;
-  if (search != LAGP_EXHAUSTIVE && search != LAGP_RAY) return false;
+  if (search != LAGP_EXHAUSTIVE && search != LAGP_RAY && search != LAGP_RAY_FULL) return false;
   if (precision != LAGP_FP64 && precision != LAGP_FP32_SCORE && precision != LAGP_FP32_SCORE_TC)
     return false;
   if (N > (int64_t)0x7fffff00) return false;   // int32 design indices
   int R = nrays <= 0 ? p : nrays;
-  if (!knn_only && search == LAGP_RAY && (R > LAGP_MAX_RAYS || R > N_close - n)) return false;
+  if (!knn_only && search != LAGP_EXHAUSTIVE && (R > LAGP_MAX_RAYS || R > N_close - n))
+    return false;
   sh->N = N;
   sh->p = p;
   sh->PP = (p + 3) / 4 * 4;
@@ -119,7 +125,7 @@ bool make_shape(int64_t N, int p, int64_t M, int n0, int n, int N_close, int nra
   sh->n0 = n0;
   sh->n_max = n;
   sh->nc_max = N_close;
-  sh->nrays = (search == LAGP_RAY) ? R : 1;
+  sh->nrays = (search != LAGP_EXHAUSTIVE) ? R : 1;
   sh->search = search;
   sh->precision = precision;
   sh->chunk = chunk_for(M, search, precision, N_close, N);
@@ -148,7 +154,7 @@ static cudaError_t run_design(const DesignArgs& a0, int search, int precision, b
   a.order = nullptr;
   a.count = nullptr;
   cudaError_t e;
-  if (search == LAGP_RAY) {
+  if (search != LAGP_EXHAUSTIVE) {
     if (uneven && a.tune.lpt) {
       if ((e = launch_order(a, search, 0, 1, s)) != cudaSuccess) return e;
       a.order = ws.order;
@@ -190,6 +196,7 @@ static DesignArgs chunk_args(const Shape& sh, const Call& c, const Workspace& ws
   a.nc_loc = c.nclose_loc ? c.nclose_loc + c0 : nullptr; a.n0 = sh.n0; a.n_max = n;
   a.n_loc = c.n_loc ? c.n_loc + c0 : nullptr; a.theta = c.theta; a.g = c.g; a.nrays = sh.nrays;
   a.theta_loc = c.theta_loc ? c.theta_loc + c0 : nullptr;
+  a.full_scope = sh.search == LAGP_RAY_FULL ? 1 : 0;
   a.mean = c.mean + c0; a.s2 = c.s2 + c0;
   a.selected = c.selected ? c.selected + c0 * n : nullptr;
   a.tie_gap = c.tie_gap ? c.tie_gap + c0 * n : nullptr;
@@ -276,7 +283,7 @@ extern "C" int laGP_autotune(const double* design, const double* y, int64_t N, i
   int nc = 0;
   const int lpts = uneven ? 2 : 1;
   for (int l = lpts - 1; l >= 0; --l) {
-    if (search == LAGP_RAY) {
+    if (search != LAGP_EXHAUSTIVE) {
       for (int rw : {2, 1, 4}) cand[nc++] = Tune{rw, l, 1};
     } else {
       for (int occ : {1, 2}) cand[nc++] = Tune{2, l, occ};
@@ -324,7 +331,7 @@ extern "C" int laGP_autotune(const double* design, const double* y, int64_t N, i
 extern "C" int laGP_tune_get(int p, int n, int N_close, int nrays, int search, int uneven,
                              int* choice) {
   if (!choice || p < 1 || p > LAGP_MAX_P) return LAGP_ERR_INVALID;
-  const int R = (search == LAGP_RAY) ? (nrays <= 0 ? p : nrays) : 1;
+  const int R = (search != LAGP_EXHAUSTIVE) ? (nrays <= 0 ? p : nrays) : 1;
   *choice = encode_tune(lookup_tune(p, n, N_close, R, search, uneven ? 1 : 0));
   return LAGP_OK;
 }
@@ -333,8 +340,9 @@ extern "C" int laGP_tune_set(int p, int n, int N_close, int nrays, int search, i
                              int choice) {
   Tune t;
   if (!decode_tune(choice, &t) || p < 1 || p > LAGP_MAX_P) return LAGP_ERR_INVALID;
-  if (search != LAGP_EXHAUSTIVE && search != LAGP_RAY) return LAGP_ERR_INVALID;
-  const int R = (search == LAGP_RAY) ? (nrays <= 0 ? p : nrays) : 1;
+  if (search != LAGP_EXHAUSTIVE && search != LAGP_RAY && search != LAGP_RAY_FULL)
+    return LAGP_ERR_INVALID;
+  const int R = (search != LAGP_EXHAUSTIVE) ? (nrays <= 0 ? p : nrays) : 1;
   store_tune(p, n, N_close, R, search, uneven ? 1 : 0, t);
   return LAGP_OK;
 }

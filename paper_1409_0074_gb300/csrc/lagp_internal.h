@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "kdtree.cuh"
+
 namespace lagp {
 
 // Device buffers carved out of the caller's workspace.  Per-location arrays
@@ -34,6 +36,7 @@ struct Workspace {
   unsigned* order_hist; // [2][256] cost-bucket counts, then offsets
   unsigned* order_count;// [2] items per part
   uint16_t* order_key;  // [chunk] part and cost bucket
+  KdTree kd;            // k-d tree over the design (LAGP_RAY_FULL; kd.perm null otherwise)
   int64_t chunk;
 };
 
@@ -139,6 +142,7 @@ struct DesignArgs {
   double theta, g;
   const double* theta_loc; // chunk-offset per-location lengthscale, or null (theta)
   int nrays;
+  int full_scope;          // ray snaps over all of X_N (LAGP_RAY_FULL)
   double* mean;            // chunk-offset outputs
   double* s2;
   int32_t* selected;       // [M][n_max] or null

@@ -24,8 +24,10 @@
 // it stays within a few hundred MB (L2-resident for moderate grids) however
 // many locations a launch covers.
 #include <cstdint>
+#include <cstring>
 
 #include "common.cuh"
+#include "kdtree.cuh"
 #include "lagp_internal.h"
 
 namespace lagp {
@@ -61,6 +63,8 @@ struct RayParams {
   unsigned* queue;      // work counter (zero at launch)
   const int32_t* order; // item -> location, or null (identity)
   const unsigned* count;// number of items (device), or null (M)
+  int full;             // snap over all of X_N through the k-d tree
+  KdView<float> kd;     // the tree in centred FP32 coordinates (full scope)
 };
 
 // start of row i in the zero-padded FP32 row storage (rows of length
@@ -79,7 +83,7 @@ __device__ __host__ __forceinline__ int kz_ld(int n) {
 }
 
 struct WarpLayout {
-  int lf, kz, zf, sf, ae, x, sel, starts, mask, smask, bytes;
+  int lf, kz, zf, sf, ae, x, sel, gsel, stk, starts, mask, smask, bytes;
 };
 
 __host__ __device__ inline WarpLayout warp_layout(int n, int PP, int RP, int nc) {
@@ -93,6 +97,8 @@ __host__ __device__ inline WarpLayout warp_layout(int n, int PP, int RP, int nc)
   w.ae = take(2 * RP * PP);
   w.x = take(4 * PP);          // xf, lof, hif, xs
   w.sel = take(n);
+  w.gsel = take(n);            // design indices of the selected points
+  w.stk = take(KD_STACK);      // k-d tree walk (full scope)
   w.starts = take(RP);
   w.mask = take((nc + 31) / 32);
   w.smask = take((nc + 31) / 32);
@@ -187,7 +193,9 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
   float* lof = xf + PP;
   float* hif = lof + PP;
   float* xs = hif + PP;
-  int* sel = reinterpret_cast<int*>(base + lay.sel);
+  int* sel = reinterpret_cast<int*>(base + lay.sel);      // candidate ranks (-1: not one)
+  int* gsel = reinterpret_cast<int*>(base + lay.gsel);    // design indices
+  int* stk = reinterpret_cast<int*>(base + lay.stk);
   int* starts = reinterpret_cast<int*>(base + lay.starts);
   uint32_t* mask = reinterpret_cast<uint32_t*>(base + lay.mask);     // selected candidates
   uint32_t* smask = reinterpret_cast<uint32_t*>(base + lay.smask);   // this step's ray starts
@@ -221,11 +229,11 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
   int j = 0;
   bool ok = (n >= P.n0) && (n <= nc) && (n <= ldn);
 
-  // ---- append candidate rank rr to the design (FP64 factor row) ----
-  auto add_point = [&](int rr) -> bool {
-    const double* c64 = P.X + (int64_t)cl[rr] * p;
+  // ---- append design point gi (candidate rank rr, or -1) (FP64 factor row) ----
+  auto add_point = [&](int gi, int rr) -> bool {
+    const double* c64 = P.X + (int64_t)gi * p;
     for (int i = lane; i <= j; i += 32) {
-      if (i < j) kv64[i] = corr64_fast(P.X + (int64_t)cl[sel[i]] * p, c64, p, nit64);
+      if (i < j) kv64[i] = corr64_fast(P.X + (int64_t)gsel[i] * p, c64, p, nit64);
       else kx64[j] = corr64_fast(c64, xq, p, nit64);
     }
     __syncwarp();
@@ -267,19 +275,20 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
       Lj[j] = inv_d;
       Lfj[j] = (float)inv_d;
       sel[j] = rr;
-      mask[rr >> 5] |= 1u << (rr & 31);
+      gsel[j] = gi;
+      if (rr >= 0) mask[rr >> 5] |= 1u << (rr & 31);
       const double zj = (kx64[j] - lz) * inv_d;
       z64[j] = zj;
-      zy64[j] = (P.Y[cl[rr]] - lzy) * inv_d;
+      zy64[j] = (P.Y[gi] - lzy) * inv_d;
       zf[j] = (float)zj;
     }
-    if (lane < PP) Sf[j * PP + lane] = P.Xf[(int64_t)cl[rr] * PP + lane];
+    if (lane < PP) Sf[j * PP + lane] = P.Xf[(int64_t)gi * PP + lane];
     __syncwarp();
     ++j;
     return true;
   };
 
-  for (int rr = 0; rr < P.n0 && ok; ++rr) ok = add_point(rr);
+  for (int rr = 0; rr < P.n0 && ok; ++rr) ok = add_point(cl[rr], rr);
 
   const int r = lane / G, q = lane % G;
   for (int step = P.n0; step < n && ok; ++step) {
@@ -460,7 +469,42 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
     for (int k = 0; k < PP; k += 2) nx[k / 2] = make_float2(-xs[k], -xs[k + 1]);
     float bd0 = __int_as_float(0x7f800000), bd1 = bd0;
     int bi0 = 0x7fffffff, bi1 = 0x7fffffff;
-    {
+    int pick_g = -1;                  // the full scope's pick (design index)
+    if (P.full) {
+      // nearest point of X_N outside the design; the step's starts are
+      // forbidden unless they equal x*
+      const KdView<float>& V = P.kd;
+      auto excluded = [&](int32_t gi, int64_t pos, bool allow_starts) -> bool {
+        for (int i = 0; i < j; ++i) if (gsel[i] == gi) return true;
+        if (allow_starts) return false;
+        for (int t = 0; t < R; ++t) {
+          if (cl[starts[t]] != gi) continue;
+          for (int k = 0; k < p; ++k) if (V.pts[pos * PP + k] != xs[k]) return true;
+        }
+        return false;
+      };
+      auto dist = [&](int64_t pos, int32_t) -> float {
+        const float* c = V.pts + pos * PP;
+        float2 d2 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < PP; k += 4) {
+          const float4 cv = *reinterpret_cast<const float4*>(c + k);
+          const float2 t01 = __fadd2_rn(make_float2(cv.x, cv.y), nx[k / 2]);
+          const float2 t23 = __fadd2_rn(make_float2(cv.z, cv.w), nx[k / 2 + 1]);
+          d2 = __ffma2_rn(t01, t01, d2);
+          d2 = __ffma2_rn(t23, t23, d2);
+        }
+        return d2.x + d2.y;
+      };
+      auto distx = [&](int64_t pos, int32_t) -> float {
+        const float* c = V.pts + pos * PP;
+        float d = 0.f;
+        for (int k = 0; k < PP; ++k) { const float t = c[k] - xf[k]; d = fmaf(t, t, d); }
+        return d;
+      };
+      const KdTop<float> b = kd_nearest<float>(V, xs, 1e-5f, stk, excluded, dist, distx);
+      pick_g = b.i1;
+    } else {
       // When the best ray kept s = 0, x* is its start, an allowed candidate at
       // distance 0; only a lower-ranked candidate at distance 0 (the same FP32
       // coordinates) could take it, so the scan stops at the start's rank.
@@ -498,7 +542,18 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
       if (od0 < bd0 || (od0 == bd0 && oi0 < bi0)) { bd0 = od0; bi0 = oi0; }
       if (od1 < bd1 || (od1 == bd1 && oi1 < bi1)) { bd1 = od1; bi1 = oi1; }
     }
-    const int pick = bi0 != 0x7fffffff ? bi0 : (bi1 != 0x7fffffff ? bi1 : -1);
+    int pick = -1;
+    if (!P.full) {
+      pick = bi0 != 0x7fffffff ? bi0 : (bi1 != 0x7fffffff ? bi1 : -1);
+      pick_g = pick >= 0 ? cl[pick] : -1;
+    } else if (pick_g >= 0) {
+      // its candidate rank, when it is one
+      int rk = 0x7fffffff;
+      for (int rr = lane; rr < nc; rr += 32) if (cl[rr] == pick_g) rk = min(rk, rr);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) rk = min(rk, __shfl_xor_sync(0xffffffffu, rk, o));
+      pick = rk != 0x7fffffff ? rk : -1;
+    }
     __syncwarp();
     if (lane < R) smask[starts[lane] >> 5] = 0u;
     if (lane == 0) {
@@ -506,7 +561,7 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
           (best > 0.f && R > 1) ? (double)((best - second) / best) : 0.0;
       if (P.nevals) P.nevals[loc * ldn + (step - P.n0)] = ev;
     }
-    ok = (pick >= 0) && add_point(pick);
+    ok = (pick_g >= 0) && add_point(pick_g, pick);
   }
 
   if (ok) {
@@ -529,7 +584,7 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
     atomicOr(P.status, LAGP_DEV_BAD_UPDATE);
   }
   if (P.selected)
-    for (int i = lane; i < ldn; i += 32) P.selected[loc * ldn + i] = (i < j) ? cl[sel[i]] : -1;
+    for (int i = lane; i < ldn; i += 32) P.selected[loc * ldn + i] = (i < j) ? gsel[i] : -1;
 }
 
 // at least 20 resident warps per SM (at most 102 registers per thread)
@@ -583,6 +638,14 @@ cudaError_t launch_ray32(const DesignArgs& a, cudaStream_t s) {
   P.selected = a.selected; P.tie_gap = a.tie_gap; P.nevals = a.nevals; P.g64 = a.ws->state64;
   P.g64_stride = (int64_t)ray32_g64_doubles(a.n_max); P.status = a.ws->status;
   P.queue = a.ws->queue; P.order = a.order; P.count = a.count;
+  P.full = a.full_scope;
+  if (P.full) {
+    const KdTree& t = a.ws->kd;
+    P.kd.box = t.box32; P.kd.stride = a.PP; P.kd.p = a.p; P.kd.D = t.D; P.kd.N = a.N;
+    P.kd.perm = t.perm; P.kd.pts = t.pts32; P.kd.by_design = false;
+  } else {
+    std::memset(&P.kd, 0, sizeof(P.kd));
+  }
   int RP = 2;
   while (RP < a.nrays) RP <<= 1;
   const WarpLayout lay = warp_layout(a.n_max, a.PP, RP, a.nc_max);

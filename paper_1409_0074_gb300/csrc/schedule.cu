@@ -65,7 +65,8 @@ __global__ void order_key_kernel(const int32_t* __restrict__ n_loc,
   const float nf = (float)(n > 1 ? n : 1), ncf = (float)(nc > 1 ? nc : 1);
   // ray: evaluations (~20 per ray step) of O(j^2) plus an O(N') snap per step;
   // exhaustive: N' candidates of O(j^2) per step
-  const float cost = (search == LAGP_RAY) ? nf * nf * nf * 7.f + nf * ncf : nf * nf * nf * ncf;
+  const float cost = (search != LAGP_EXHAUSTIVE) ? nf * nf * nf * 7.f + nf * ncf
+                                                 : nf * nf * nf * ncf;
   int b = lpt ? (int)floorf(8.f * log2f(cost)) : 0;
   b = b < 0 ? 0 : (b > 255 ? 255 : b);
   const int part = (split_n > 0 && n > split_n) ? 1 : 0;

@@ -13,9 +13,9 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblagp_gb300.so")
 
-LAGP_EXHAUSTIVE, LAGP_RAY = 0, 1
+LAGP_EXHAUSTIVE, LAGP_RAY, LAGP_RAY_FULL = 0, 1, 2
 LAGP_FP64, LAGP_FP32_SCORE, LAGP_FP32_SCORE_TC = 0, 1, 2
-SEARCH = {"exhaustive": LAGP_EXHAUSTIVE, "ray": LAGP_RAY}
+SEARCH = {"exhaustive": LAGP_EXHAUSTIVE, "ray": LAGP_RAY, "ray_full": LAGP_RAY_FULL}
 PRECISION = {"fp64": LAGP_FP64, "fp32": LAGP_FP32_SCORE, "fp32_tc": LAGP_FP32_SCORE_TC}
 ERRORS = {-1: "invalid argument", -2: "workspace too small", -3: "CUDA error",
           -4: "device reported a failure"}

@@ -49,7 +49,7 @@ def test_workspace_sizes_and_argument_checks(lib):
         (100000, 4, 10, 129, 1000, 4, 1, 0),     # n > 128
         (100000, 4, 10, 50, 1000, 17, 1, 0),     # too many rays
         (100000, 4, 10, 50, 52, 4, 1, 0),        # nrays > N_close - n
-        (100000, 4, 10, 50, 1000, 4, 2, 0),      # bad search
+        (100000, 4, 10, 50, 1000, 4, 3, 0),      # bad search
         (100000, 4, 10, 50, 1000, 4, 1, 3),      # bad precision
         (100000, 4, 10, 50, 1000, 4, 1, -1),     # bad precision
     ]
