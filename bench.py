@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--M", type=int, default=100_000)
     ap.add_argument("--N", type=int, default=1_000_000)
-    ap.add_argument("--search", default="ray", choices=["ray", "exhaustive"])
+    ap.add_argument("--search", default="ray", choices=["ray", "exhaustive", "ray_full"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_tc", "fp64"])
     ap.add_argument("--no-extras", action="store_true", help="skip the other search/precision forms")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
@@ -697,8 +697,33 @@ def request_breakdown(ctx, w, M, rng, repeats=5):
             "device_ms": float(sum(v[0] for v in prof.values()))}
 
 
-def run_serving(args, rates32=(50.0, 200.0, 400.0, 600.0, 800.0, 1000.0, 1400.0),
-                rates64=(1.0, 3.0, 6.0, 10.0)):
+def mix_capacity(X, Y, w, precision, M=30_000, steps=2):
+    """Locations/s of one direct call on the served mix (n uniform over
+    {30, 50, 100}, N' = 1000, ray search with 8 rays): the device's capacity
+    for that mix, against which the served rates are read."""
+    import torch
+    from paper_1409_0074_gb300 import lagp
+    rng = np.random.default_rng(12)
+    xr = torch.from_numpy(rng.random((M, w.p))).cuda()
+    nl = torch.from_numpy(rng.choice(np.array([30, 50, 100], np.int32), M)).cuda()
+    pr = lagp.PRECISION[precision]
+    wsb = lagp.laGP_workspace_bytes(w.N, w.p, M, 100, 1000, 8, lagp.LAGP_RAY, pr)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    mean = torch.empty(M, dtype=torch.float64, device="cuda")
+    s2 = torch.empty(M, dtype=torch.float64, device="cuda")
+    go = lambda: lagp.laGP_build_and_predict(X, Y, xr, w.n0, 100, 1000, w.theta, w.g,
+                                             lagp.LAGP_RAY, 8, pr, mean, s2, ws, n_loc=nl)
+    go()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        go()
+    torch.cuda.synchronize()
+    return M * steps / (time.perf_counter() - t0)
+
+
+def run_serving(args, rates32=(50.0, 100.0, 150.0, 200.0, 250.0, 300.0, 400.0),
+                rates64=(0.5, 1.0, 2.0, 4.0)):
     """Serving form: the N = 1e6, p = 8 design resident in a serving context;
     Poisson request streams of 1..4096 locations (log-uniform), n in
     {30, 50, 100}, N' = 1000, ray search with 8 rays, through the
@@ -731,11 +756,14 @@ def run_serving(args, rates32=(50.0, 200.0, 400.0, 600.0, 800.0, 1000.0, 1400.0)
                                      max_requests=3000)}
         if prec == "fp32":
             form["breakdown"] = [request_breakdown(ctx, w, M, rng) for M in (1, 64)]
-        ok = [r for r in form["rates"] if r["p99_ms"] <= 250.0]
-        form["max_locations_per_s_at_p99_le_250ms"] = (max(r["locations_per_s"] for r in ok)
-                                                       if ok else None)
-        out[prec] = form
+        for slo in (100.0, 250.0, 500.0):
+            ok = [r for r in form["rates"] if r["p99_ms"] <= slo]
+            form["max_locations_per_s_at_p99_le_%dms" % slo] = (
+                max(r["locations_per_s"] for r in ok) if ok else None)
         ctx.close()
+        form["direct_call_capacity_same_mix"] = mix_capacity(
+            X, Y, w, prec, M=30_000 if prec == "fp32" else 2000, steps=2 if prec == "fp32" else 1)
+        out[prec] = form
     return out
 
 

@@ -90,8 +90,10 @@ struct L32 {
   unsigned char* used;
   int j;
   float neg_inv_theta, onepg;
-  double nit64;              // -1 / theta of the current location
 };
+
+// lengthscale of the CTA's current location (kept out of the registers)
+static __shared__ double d32_theta;
 
 __device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -183,7 +185,7 @@ __device__ bool add_point32(const D32Params& P, L32& L, const int32_t* cl, const
   if (tid < p) L.S64[j * p + tid] = c[tid];
   if (tid < P.PP) L.Sf[j * P.PP + tid] = cand_f(P, crow, r)[tid];
   __syncthreads();
-  const double nit64 = L.nit64;
+  const double nit64 = -1.0 / d32_theta;
   // correlations of the new point with the design, and with x (thread j)
   for (int i = tid; i <= j; i += blockDim.x) {
     if (i < j) L.kvec[i] = corr64_fast(L.S64 + i * p, L.S64 + j * p, p, nit64);
@@ -329,6 +331,8 @@ __global__ void __launch_bounds__(D32_THREADS, 6) design32(D32Params P) {
   L.ired = ip; ip += 2 * D32_WARPS + 2;
   L.used = reinterpret_cast<unsigned char*>(ip);
   L.onepg = (float)(1.0 + P.g);
+  L.neg_inv_theta = (float)(-1.0 / P.theta);
+  if (threadIdx.x == 0) d32_theta = P.theta;
   const unsigned items = P.count ? *P.count : (unsigned)P.M;
   for (;;) {
     if (tid == 0) s_item = atomicAdd(P.queue, 1u);
@@ -341,9 +345,9 @@ __global__ void __launch_bounds__(D32_THREADS, 6) design32(D32Params P) {
     const int n = P.n_loc ? P.n_loc[loc] : P.n_max;
     const int32_t* cl = P.cand + loc * P.nc_max;
     L.j = 0;
-    {
-      const double th = P.theta_loc ? P.theta_loc[loc] : P.theta;
-      L.nit64 = -1.0 / th;
+    if (P.theta_loc) {
+      const double th = P.theta_loc[loc];
+      if (tid == 0) d32_theta = th;
       L.neg_inv_theta = (float)(-1.0 / th);
     }
 

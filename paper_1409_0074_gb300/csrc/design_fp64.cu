@@ -124,7 +124,8 @@ struct Loc {
   Top2* red;         // [WARPS]
   int* sel;          // [n_max] selected ranks (-1: not a candidate)
   int* gsel;         // [n_max] selected design indices
-  int* stk;          // [KD_STACK] k-d tree walk (full scope)
+  int* stk;          // [KD_STACK] k-d tree walk (full scope): nodes
+  double* bnd;       // [KD_STACK] and their box distances
   int* rnev;         // [R]
   int* starts;       // [R]
   int* iscal;        // [4]
@@ -432,7 +433,7 @@ __device__ int search_ray(const D64Params& P, Loc& L, const int32_t* cl, int nc,
       };
       auto dist = [&](int64_t, int32_t gi) { return sqdist64(P.X + (int64_t)gi * p, L.xs, p); };
       auto distx = [&](int64_t, int32_t gi) { return sqdist64(P.X + (int64_t)gi * p, L.xq, p); };
-      const KdTop<double> b = kd_nearest<double>(V, L.xs, 1e-12, L.stk, excluded, dist, distx);
+      const KdTop<double> b = kd_nearest<double>(V, L.xs, 1e-12, L.stk, L.bnd, excluded, dist, distx);
       if (lane == 0) {
         L.iscal[1] = b.i1;
         L.iscal[2] = 0x7fffffff;
@@ -556,6 +557,7 @@ __global__ void __launch_bounds__(D64_THREADS) design64(D64Params P) {
   L.rgap = dp; dp += R;
   L.xs = dp; dp += p;
   L.scal = dp; dp += 4;
+  L.bnd = dp; dp += KD_STACK;
   L.red = reinterpret_cast<Top2*>(dp); dp += 3 * D64_WARPS;
   int* ip = reinterpret_cast<int*>(dp);
   L.sel = ip; ip += ld;
@@ -614,7 +616,7 @@ __global__ void __launch_bounds__(D64_THREADS) design64(D64Params P) {
 static size_t smem_design64(int n_max, int p, int nc_max, int R) {
   size_t d = (size_t)n_max * n_max + (size_t)n_max * p + 3 * n_max + 3 * p +
              2 * D64_WARPS * n_max + D64_WARPS * p + 2 * R * p + 3 * R + p + 4 +
-             3 * D64_WARPS * ((sizeof(Top2) + 7) / 8);
+             3 * D64_WARPS * ((sizeof(Top2) + 7) / 8) + KD_STACK;
   size_t i = 2 * (size_t)n_max + KD_STACK + 2 * R + 4;
   return d * 8 + i * 4 + nc_max + 16;
 }

@@ -96,17 +96,24 @@ struct KdView {
   }
 };
 
+// Squared distances from xs to the boxes of nodes c0 = 2v and c0 + 1, one
+// half-warp per child and one lane per coordinate (p <= 16), summed by
+// shuffles; every lane receives both.
 template <typename T>
-__device__ __forceinline__ T kd_box_lb(const KdView<T>& V, int64_t v, const T* xs) {
-  const T* lo = V.box + v * 2 * V.stride;
-  const T* hi = lo + V.stride;
-  T s = 0;
-  for (int k = 0; k < V.p; ++k) {
-    const T a = lo[k] - xs[k], b = xs[k] - hi[k];
-    const T t = a > 0 ? a : (b > 0 ? b : (T)0);
-    s += t * t;
+__device__ __forceinline__ void kd_child_lbs(const KdView<T>& V, int64_t v, T xk, T* l0, T* l1) {
+  const int lane = threadIdx.x & 31, k = lane & 15;
+  const int64_t c = 2 * v + (lane >> 4);
+  T t = 0;
+  if (k < V.p) {
+    const T* lo = V.box + c * 2 * V.stride;
+    const T a = lo[k] - xk, b = xk - lo[V.stride + k];
+    t = a > 0 ? a : (b > 0 ? b : (T)0);
+    t = t * t;
   }
-  return s;
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  *l0 = __shfl_sync(0xffffffffu, t, 0);
+  *l1 = __shfl_sync(0xffffffffu, t, 16);
 }
 
 // Nearest point to xs outside the design (and its second-best distance).
@@ -114,47 +121,58 @@ __device__ __forceinline__ T kd_box_lb(const KdView<T>& V, int64_t v, const T* x
 // allow_starts) says whether design point gi (at tree position pos) may not be
 // picked; with no allowed point at all the search repeats with the ray starts
 // allowed.  dist(pos, gi) and distx(pos, gi) give a point's squared distances
-// to x* and to x in the form's own arithmetic.  stk: KD_STACK ints per warp.
+// to x* and to x in the form's own arithmetic.  stk / bnd: KD_STACK entries
+// per warp (a pending node and its box distance).
 template <typename T, typename Excl, typename Dist, typename DistX>
-__device__ KdTop<T> kd_nearest(const KdView<T>& V, const T* xs, T margin, int* stk, Excl excluded,
-                               Dist dist, DistX distx) {
+__device__ KdTop<T> kd_nearest(const KdView<T>& V, const T* xs, T margin, int* stk, T* bnd,
+                               Excl excluded, Dist dist, DistX distx) {
   const int lane = threadIdx.x & 31;
   const T inf = (T)INFINITY;
+  const T xk = (lane & 15) < V.p ? xs[lane & 15] : (T)0;
   KdTop<T> best;
   for (int pass = 0; pass < 2; ++pass) {
     best.d1 = inf; best.dx1 = inf; best.d2 = inf; best.i1 = -1;
-    int sp = 0;
-    if (lane == 0) stk[0] = 1;
-    sp = 1;
+    if (lane == 0) { stk[0] = 1; bnd[0] = 0; }
+    int sp = 1;
     __syncwarp();
     while (sp > 0) {
-      const int64_t v = stk[--sp];
+      --sp;
+      const int64_t v = stk[sp];
+      const T lbv = bnd[sp];
       __syncwarp();
+      if (lbv > best.d2 * ((T)1 + margin)) continue;
       const int level = 31 - __clz((int)v);
-      const T lb = kd_box_lb(V, v, xs);
-      if (lb > best.d2 * ((T)1 + margin)) continue;
       if (level == V.D) {
         int64_t a, b;
         kd_range(V.N, v, level, &a, &b);
         const int64_t pos = a + lane;
         KdTop<T> t;
         t.d1 = inf; t.dx1 = inf; t.d2 = inf; t.i1 = -1;
+        bool near = false;
+        T d = inf;
+        int32_t gi = -1;
         if (pos < b) {
-          const int32_t gi = V.perm[pos];
-          const T d = dist(pos, gi);
-          if (d <= best.d2 && !excluded(gi, pos, pass == 1)) {
-            t.d1 = d;
-            t.dx1 = distx(pos, gi);
-            t.i1 = gi;
-          }
+          gi = V.perm[pos];
+          d = dist(pos, gi);
+          near = d <= best.d2;
+        }
+        // most leaves hold no point nearer than the second best: no merge
+        if (!__any_sync(0xffffffffu, near)) continue;
+        if (near && !excluded(gi, pos, pass == 1)) {
+          t.d1 = d;
+          t.dx1 = distx(pos, gi);
+          t.i1 = gi;
         }
         best = kd_merge(best, kd_warp_merge(t));
       } else {
-        const T l0 = kd_box_lb(V, 2 * v, xs), l1 = kd_box_lb(V, 2 * v + 1, xs);
-        const int64_t nearer = l1 < l0 ? 2 * v + 1 : 2 * v;
+        T l0, l1;
+        kd_child_lbs(V, v, xk, &l0, &l1);
+        const bool right_first = l1 < l0;
         if (lane == 0) {
-          stk[sp] = (int)(nearer ^ 1);
-          stk[sp + 1] = (int)nearer;
+          stk[sp] = (int)(2 * v + (right_first ? 0 : 1));
+          bnd[sp] = right_first ? l0 : l1;
+          stk[sp + 1] = (int)(2 * v + (right_first ? 1 : 0));
+          bnd[sp + 1] = right_first ? l1 : l0;
         }
         sp += 2;
         __syncwarp();

@@ -201,8 +201,8 @@ knn_tc(const float* __restrict__ Btiles, int64_t ntiles, int p, const double* __
   const int64_t q0 = (int64_t)blockIdx.x * KT_M;
   // design segment of this CTA: tiles [t_lo, t_lo + nt) (the whole design
   // unless the launch splits it over gridDim.y CTAs per location tile)
-  const int64_t t_lo = (int64_t)blockIdx.y * ntiles / gridDim.y;
-  const int64_t nt = (int64_t)(blockIdx.y + 1) * ntiles / gridDim.y - t_lo;
+  const int64_t t_lo = SPLIT ? (int64_t)blockIdx.y * ntiles / gridDim.y : 0;
+  const int64_t nt = SPLIT ? (int64_t)(blockIdx.y + 1) * ntiles / gridDim.y - t_lo : ntiles;
   const float rdes = sqrtf(__uint_as_float(*maxn2_bits)) * 1.0001f;
   const float inf = __int_as_float(0x7f800000);
 
@@ -353,14 +353,17 @@ knn_tc(const float* __restrict__ Btiles, int64_t ntiles, int p, const double* __
         for (int u = 0; u < 64; ++u) {
           const float d = __uint_as_float(v[u]);
           if (d <= keep) {
-            KnnEntry e;
-            e.d = fmaxf(d, 0.f);
-            e.idx = pbase + c0 + u;
             if (SPLIT) {
               // segments of one location share its buffer through a counter
+              KnnEntry e;
+              e.d = fmaxf(d, 0.f);
+              e.idx = pbase + c0 + u;
               const int slot = atomicAdd(&seg_out[q * KT_GROUPS], 1);
               if (slot < cap) buf[q * (int64_t)cap + slot] = e;
             } else if (mycnt < seg) {
+              KnnEntry e;
+              e.d = fmaxf(d, 0.f);
+              e.idx = pbase + c0 + u;
               qb[mycnt] = e;
             }
             ++mycnt;

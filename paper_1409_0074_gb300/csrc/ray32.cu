@@ -83,7 +83,7 @@ __device__ __host__ __forceinline__ int kz_ld(int n) {
 }
 
 struct WarpLayout {
-  int lf, kz, zf, sf, ae, x, sel, gsel, stk, starts, mask, smask, bytes;
+  int lf, kz, zf, sf, ae, x, sel, gsel, stk, bnd, starts, mask, smask, bytes;
 };
 
 __host__ __device__ inline WarpLayout warp_layout(int n, int PP, int RP, int nc) {
@@ -98,7 +98,8 @@ __host__ __device__ inline WarpLayout warp_layout(int n, int PP, int RP, int nc)
   w.x = take(4 * PP);          // xf, lof, hif, xs
   w.sel = take(n);
   w.gsel = take(n);            // design indices of the selected points
-  w.stk = take(KD_STACK);      // k-d tree walk (full scope)
+  w.stk = take(KD_STACK);      // k-d tree walk (full scope): nodes
+  w.bnd = take(KD_STACK);      // and their box distances
   w.starts = take(RP);
   w.mask = take((nc + 31) / 32);
   w.smask = take((nc + 31) / 32);
@@ -196,6 +197,7 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
   int* sel = reinterpret_cast<int*>(base + lay.sel);      // candidate ranks (-1: not one)
   int* gsel = reinterpret_cast<int*>(base + lay.gsel);    // design indices
   int* stk = reinterpret_cast<int*>(base + lay.stk);
+  float* bnd = base + lay.bnd;
   int* starts = reinterpret_cast<int*>(base + lay.starts);
   uint32_t* mask = reinterpret_cast<uint32_t*>(base + lay.mask);     // selected candidates
   uint32_t* smask = reinterpret_cast<uint32_t*>(base + lay.smask);   // this step's ray starts
@@ -502,7 +504,7 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
         for (int k = 0; k < PP; ++k) { const float t = c[k] - xf[k]; d = fmaf(t, t, d); }
         return d;
       };
-      const KdTop<float> b = kd_nearest<float>(V, xs, 1e-5f, stk, excluded, dist, distx);
+      const KdTop<float> b = kd_nearest<float>(V, xs, 1e-5f, stk, bnd, excluded, dist, distx);
       pick_g = b.i1;
     } else {
       // When the best ray kept s = 0, x* is its start, an allowed candidate at
