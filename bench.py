@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--M", type=int, default=100_000)
     ap.add_argument("--N", type=int, default=1_000_000)
     ap.add_argument("--search", default="ray", choices=["ray", "exhaustive", "ray_full"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_tc", "fp64"])
+    ap.add_argument("--precision", default="fp32",
+                    choices=["fp32", "fp32_tc", "fp64", "fp32_promote", "fp32_tc_promote"])
     ap.add_argument("--no-extras", action="store_true", help="skip the other search/precision forms")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle locations (0: 32 per core)")
@@ -378,6 +379,7 @@ def run_ours(args, rank, world):
     rc, st = lagp.laGP_status(ws)
     if rc != 0:
         raise RuntimeError("device status %d in the timed region" % st)
+    promoted = lagp.laGP_promoted(ws)    # of the last timed step
 
     # dominant kernel and its roofline
     top = max(prof.items(), key=lambda kv: kv[1][0])
@@ -397,6 +399,7 @@ def run_ours(args, rank, world):
     return dict(value=value, ms=ms_max, clocks=clk.summary(), roofline=roof, kernels=kernels,
                 gpu_launches=int(sum(v[1] for v in prof.values())), w=w, tensors=(X, Y, Xr),
                 evals_per_step=mean_evals, max_evals_per_step=float(nev.max()),
+                promoted=promoted,
                 rmse=float(np.sqrt(np.mean((mean.cpu().numpy() - w.Ytrue) ** 2))))
 
 
@@ -467,9 +470,53 @@ def run_extra(args, w, tensors, search, precision, M, steps=2):
         ev = {k: v / chunks for k, v in eval_sums(nv, w.n0).items()}
     rmse = float(np.sqrt(np.mean((mean.cpu().numpy() - w.Ytrue[:M]) ** 2)))
     return {"locations_per_s": M * steps / (e0.elapsed_time(e1) / 1e3), "locations": M,
-            "rmse": rmse, "roofline": roofline(name, tot_ms, launches, w, M / chunks, ev),
+            "rmse": rmse, "promoted_locations": lagp.laGP_promoted(ws),
+            "roofline": roofline(name, tot_ms, launches, w, M / chunks, ev),
             "kernels": {k: {"ms_per_step": v[0] / steps, "launches": v[1]}
                         for k, v in prof.items()}}
+
+
+def run_prescaled(args, w, tensors, n_sub=1000, steps=2):
+    """Rays with pre-scaled inputs (Sec 5.3): the separable global lengthscales
+    on a random 1,000-row subset (laGP_sep_mle), the design and locations
+    divided by their square roots (laGP_prescale), then the FP32 ray path at
+    theta = 1 on the scaled inputs over all locations.  Reports the fit's time
+    and iterations, the estimate, and locations/s and RMSE of the local path."""
+    import time
+    import torch
+    from paper_1409_0074_gb300 import lagp
+    from paper_1409_0074_gb300 import workloads as W
+    X, Y, Xr = tensors
+    sub = torch.from_numpy(W.subset(w.N, n_sub, seed=1)).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    th, (it, ev, st) = lagp.sep_mle(X, Y, sub, w.g, 1.0, 1e-3, 100.0)
+    fit_s = time.perf_counter() - t0
+    Xs, Xrs = lagp.prescale(X, th), lagp.prescale(Xr, th)
+    M = Xr.shape[0]
+    s, pr = lagp.SEARCH["ray"], lagp.PRECISION["fp32"]
+    wsb = lagp.laGP_workspace_bytes(w.N, w.p, M, w.n, w.nc, w.nrays, s, pr)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    mean = torch.empty(M, dtype=torch.float64, device="cuda")
+    s2 = torch.empty(M, dtype=torch.float64, device="cuda")
+    go = lambda: lagp.laGP_build_and_predict(Xs, Y, Xrs, w.n0, w.n, w.nc, 1.0, w.g, s, w.nrays,
+                                             pr, mean, s2, ws)
+    go()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        go()
+    e1.record()
+    torch.cuda.synchronize()
+    rc, stt = lagp.laGP_status(ws)
+    if rc != 0:
+        raise RuntimeError("device status %d in the pre-scaled form" % stt)
+    return {"subset": n_sub, "fit_seconds": fit_s, "fit_iterations": it,
+            "fit_evaluations": ev, "theta_global": [float(v) for v in th.cpu()],
+            "search": "ray", "precision": "fp32 scoring", "theta_local": 1.0,
+            "locations": M, "locations_per_s": M * steps / (e0.elapsed_time(e1) / 1e3),
+            "rmse": float(np.sqrt(np.mean((mean.cpu().numpy() - w.Ytrue[:M]) ** 2)))}
 
 
 def run_nrays_sweep(args, w, tensors, M=20_000, steps=2):
@@ -527,7 +574,7 @@ def run_paper_2d(args, steps=2):
            "theta0": w.theta, "g": w.g, "forms": {}}
     rmse = lambda t: float(np.sqrt(np.mean((t.cpu().numpy() - w.Ytrue) ** 2)))
     for search in ("ray", "exhaustive"):
-        for prec in ("fp32", "fp64"):
+        for prec in ("fp32", "fp32_promote", "fp64"):
             s, pr = lagp.SEARCH[search], lagp.PRECISION[prec]
             wsb = lagp.laGP_workspace_bytes(w.N, w.p, w.M, w.n, w.nc, 1, s, pr)
             ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
@@ -548,7 +595,7 @@ def run_paper_2d(args, steps=2):
             if rc != 0:
                 raise RuntimeError("device status %d in the 2-d form" % st)
             f = {"locations_per_s": w.M * steps / (e0.elapsed_time(e1) / 1e3),
-                 "rmse_theta0": rmse(mean)}
+                 "rmse_theta0": rmse(mean), "promoted_locations": lagp.laGP_promoted(ws)}
             if prec == "fp64" and search == "ray":
                 # the local estimate alone, on these designs: its roofline
                 th = torch.empty(w.M, dtype=torch.float64, device=dev)
@@ -843,7 +890,8 @@ def main():
                  "roofline": r["roofline"], "clocks": r["clocks"],
                  "gpu_launches": r["gpu_launches"], "kernels": r["kernels"],
                  "rmse": r["rmse"], "ray_evals_per_step": r["evals_per_step"],
-                 "ray_evals_per_step_max": r["max_evals_per_step"]})
+                 "ray_evals_per_step_max": r["max_evals_per_step"],
+                 "promoted_locations_per_step": r["promoted"]})
     if world == 1:
         line["e2e"] = run_e2e(args, w)
         if not args.no_extras:
@@ -851,6 +899,8 @@ def main():
             ex["exhaustive_fp32"] = run_extra(args, w, r["tensors"], "exhaustive", "fp32", w.M)
             ex["exhaustive_fp32_tc"] = run_extra(args, w, r["tensors"], "exhaustive", "fp32_tc",
                                                  w.M)
+            ex["ray_fp32_promote"] = run_extra(args, w, r["tensors"], "ray", "fp32_promote",
+                                               w.M)
             ex["ray_fp64"] = run_extra(args, w, r["tensors"], "ray", "fp64", min(w.M, 4000))
             ex["ray_full_scope_fp32"] = run_extra(args, w, r["tensors"], "ray_full", "fp32", w.M)
             ex["ray_full_scope_fp64"] = run_extra(args, w, r["tensors"], "ray_full", "fp64",
@@ -859,6 +909,7 @@ def main():
                                               min(w.M, 1000), steps=1)
             line["other_forms"] = ex
             line["nrays_sweep"] = run_nrays_sweep(args, w, r["tensors"])
+            line["prescaled_form"] = run_prescaled(args, w, r["tensors"])
             line["paper_2d_form"] = run_paper_2d(args)
         if not args.no_batching:
             line["batching_form"] = run_batching(args)

@@ -67,10 +67,30 @@ extern "C" {
  *   W = Kc L_j^{-T} at every step as a dense contraction on the tensor cores
  *   (3xTF32 split products, FP32 accumulation) for local designs up to 64
  *   points (larger ones as LAGP_FP32_SCORE).  Same method and tolerances,
- *   other rounding; ray search is the same as LAGP_FP32_SCORE. */
+ *   other rounding; ray search is the same as LAGP_FP32_SCORE.
+ *
+ * LAGP_PROMOTE, OR-ed into either FP32 form: precision promotion.  Every form
+ * computes the Schur complements v = 1 + g - k^T K_j^{-1} k of the points a
+ * location adds (the pivots of the partitioned update, Sec 2.2) in binary64.
+ * The FP32 estimate of a candidate's v carries an absolute error of a few
+ * 1e-7 (FP32 rounding of the correlations and of L_j^{-1}), so once a local
+ * design's pivots fall to a few 1e-5 the FP32 scores no longer rank the
+ * candidates.  With LAGP_PROMOTE, a location whose smallest pivot is below
+ * LAGP_PROMOTE_PIVOT is solved again within the same call by the binary64
+ * kernels (its results then equal those of LAGP_FP64) and its FP32 results
+ * are overwritten.  Measured on seeded uniform designs: the 8-d, N = 1e6,
+ * theta = 1 workload meets the FP32 accuracy bar without it and would promote
+ * about 3 in 10,000 ray locations (a binary64 ray location takes ~29 ms on
+ * its own, a tail added to the call); the 4-d, N = 1e5, theta = 0.25 workload
+ * has smallest pivots of 1.5e-6 .. 8.4e-6, where the FP32 choice differed
+ * from the binary64 one at 17 to 29 of the 44 greedy steps of every location,
+ * and is promoted whole.  laGP_promoted reports how many locations the last
+ * call promoted. */
 #define LAGP_FP64 0
 #define LAGP_FP32_SCORE 1
 #define LAGP_FP32_SCORE_TC 2
+#define LAGP_PROMOTE 16
+#define LAGP_PROMOTE_PIVOT 3e-5
 
 /* Return codes. */
 #define LAGP_OK 0
@@ -110,7 +130,8 @@ size_t laGP_workspace_bytes(int64_t N, int p, int64_t M, int n, int N_close, int
  *   search    LAGP_EXHAUSTIVE, LAGP_RAY or LAGP_RAY_FULL
  *   nrays     rays per step of a ray search (<= 0 selects p; at most 16 and at
  *             most N_close - n); ignored for LAGP_EXHAUSTIVE
- *   precision LAGP_FP64, LAGP_FP32_SCORE or LAGP_FP32_SCORE_TC
+ *   precision LAGP_FP64, LAGP_FP32_SCORE or LAGP_FP32_SCORE_TC, the FP32 forms
+ *             optionally OR-ed with LAGP_PROMOTE
  *   n_loc     device [M] int32 or NULL: per-location final size (each in
  *             [n0, n]); NULL gives every location n
  *   nclose_loc device [M] int32 or NULL: per-location N_close (each in
@@ -250,12 +271,68 @@ int laGP_build_and_predict_mle(const double* design, const double* y, int64_t N,
                                size_t workspace_bytes, void* stream);
 
 /*
+ * Pre-scaled inputs (Sec 5.3, the subset table's "rays with pre-scaled
+ * inputs"): a crude global analysis fits a separable Gaussian correlation
+ * K_ab = exp(-sum_k (x_ak - x_bk)^2 / theta_k), diagonal 1 + g, to a random
+ * subset of the design by maximum likelihood (the reference-prior likelihood
+ * of Eq. gpk, as for the local lengthscale, with one theta per input), and
+ * every input coordinate is then divided by sqrt(theta_k); the local
+ * approximation runs on the scaled design and locations with theta = 1, the
+ * global correlation in scaled coordinates.
+ *
+ * laGP_sep_mle_workspace_bytes: device workspace of laGP_sep_mle for a
+ * subset of n_sub rows (2 <= n_sub <= 1024) in p <= 16 inputs (0 otherwise);
+ * about 8 n_sub^2 bytes.
+ *
+ * laGP_sep_mle: the fit on the design rows subset[0 .. n_sub - 1].
+ *   design, y  device [N][p], [N] (as in laGP_build_and_predict)
+ *   subset     device [n_sub] int32 row indices (the caller's random draw)
+ *   g          fixed nugget (>= 0)
+ *   theta0     start, the same for every input (> 0)
+ *   tmin, tmax the box of every theta_k (0 < tmin <= tmax)
+ *   maxit      iterations at most (>= 1)
+ *   theta_out  device [p]: the estimate
+ *   info       device [3] int32 or NULL: iterations, likelihood evaluations,
+ *              status (0 ok, 1 the start's K not positive definite, 2 a
+ *              subset index outside [0, N))
+ * Maximiser: BFGS on log theta from log theta0 with an Armijo line search
+ * (halvings from a step capped at 2 per coordinate), projected on the box,
+ * ending when a step moves no coordinate by more than 1e-9.  Each likelihood
+ * evaluation inverts K by Gauss-Jordan elimination (K is positive definite;
+ * its pivots give log|K|).  Unlike the other entry points this one blocks:
+ * it synchronises `stream` after every evaluation to read the done flag.
+ * Returns LAGP_OK, LAGP_ERR_INVALID / _WORKSPACE for bad arguments,
+ * LAGP_ERR_CUDA, or LAGP_ERR_DEVICE when the status is not 0.
+ *
+ * laGP_prescale: X_out[r][k] = X[r][k] / sqrt(theta[k]) for rows r < rows
+ * (device arrays; X_out may be X).  Returns LAGP_OK, LAGP_ERR_INVALID or
+ * LAGP_ERR_CUDA.
+ */
+size_t laGP_sep_mle_workspace_bytes(int n_sub, int p);
+int laGP_sep_mle(const double* design, const double* y, int64_t N, int p, const int32_t* subset,
+                 int n_sub, double g, double theta0, double tmin, double tmax, int maxit,
+                 double* theta_out, int32_t* info, void* workspace, size_t workspace_bytes,
+                 void* stream);
+int laGP_prescale(const double* X, int64_t rows, int p, const double* theta, double* X_out,
+                  void* stream);
+
+/*
  * Waits for `stream`, then reads and clears the device status word of the
  * workspace.  *status receives the LAGP_STATUS_* bits.  Returns LAGP_OK when
  * no bit was set, LAGP_ERR_DEVICE when one was, LAGP_ERR_CUDA when the wait
  * or the copy failed.
  */
 int laGP_status(void* workspace, void* stream, unsigned* status);
+
+/*
+ * Waits for `stream`, then reads how many locations the last call on this
+ * workspace (laGP_build_and_predict, its plan replay or host form,
+ * laGP_build_and_predict_mle: every design pass counts) handed to the
+ * binary64 re-solve of LAGP_PROMOTE (0 without the flag).  Each call resets
+ * the count when it starts.  Returns LAGP_OK, or LAGP_ERR_INVALID for a NULL
+ * argument, LAGP_ERR_CUDA when the copy failed.
+ */
+int laGP_promoted(void* workspace, void* stream, int64_t* count);
 
 /*
  * Host-buffer form of laGP_build_and_predict: design, y, xref, n_loc,

@@ -31,6 +31,7 @@ UNITS = {
     "serve.cu": [],
     "mle.cu": [],
     "kdtree.cu": [],
+    "prescale.cu": [],
 }
 
 

@@ -16,7 +16,24 @@
 // Bound of every mbarrier wait, in SM clock cycles (about 2 s at 2 GHz).
 #define LAGP_WAIT_CYCLES 4000000000ll
 
+// Smallest binary64 pivot below which an FP32-scoring location is solved
+// again in binary64 under precision promotion (the reasoning is with
+// LAGP_PROMOTE in lagp.h).
+#define LAGP_PROMOTE_PIVOT_DEV 3e-5
+
 namespace lagp {
+
+// Precision promotion: one thread per location appends `loc` to the list
+// of binary64 re-solves when the smallest pivot v of its local design is below
+// the threshold (or not a number).  count[0] indexes the list of this launch,
+// count[1] totals the call.  list == null: promotion is off.
+__device__ __forceinline__ void promote_location(int32_t* list, unsigned* count, int64_t loc,
+                                                 double vmin) {
+  if (list && !(vmin >= LAGP_PROMOTE_PIVOT_DEV)) {
+    list[atomicAdd(count, 1u)] = (int32_t)loc;
+    atomicAdd(count + 1, 1u);
+  }
+}
 
 // exp(x) in binary64 by Cody & Waite (1980) argument reduction x = k ln2 + r,
 // |r| <= ln2/2, the degree-13 Taylor polynomial of e^r by Horner's rule, and an

@@ -66,6 +66,8 @@ struct D32Params {
   unsigned* queue;       // work counter (zero at launch)
   const int32_t* order;  // item -> location, or null
   const unsigned* count; // items (device), or null (M)
+  int32_t* promote;      // binary64 re-solve list, or null (promotion off)
+  unsigned* promote_count;
 };
 
 struct L32 {
@@ -92,8 +94,10 @@ struct L32 {
   float neg_inv_theta, onepg;
 };
 
-// lengthscale of the CTA's current location (kept out of the registers)
+// lengthscale of the CTA's current location, and the smallest binary64 pivot
+// of its local design (kept out of the registers)
 static __shared__ double d32_theta;
+static __shared__ double d32_vmin;
 
 __device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -204,6 +208,7 @@ __device__ bool add_point32(const D32Params& P, L32& L, const int32_t* cl, const
   if (tid == 0) {
     const double v = (1.0 + P.g) - vv;
     piv[0] = v;
+    if (P.promote) d32_vmin = v > 0.0 ? fmin(d32_vmin, v) : -1.0;
     piv[1] = v > 0.0 ? 1.0 / sqrt(v) : 0.0;
   }
   __syncthreads();
@@ -345,6 +350,7 @@ __global__ void __launch_bounds__(D32_THREADS, 6) design32(D32Params P) {
     const int n = P.n_loc ? P.n_loc[loc] : P.n_max;
     const int32_t* cl = P.cand + loc * P.nc_max;
     L.j = 0;
+    if (tid == 0) d32_vmin = INFINITY;
     if (P.theta_loc) {
       const double th = P.theta_loc[loc];
       if (tid == 0) d32_theta = th;
@@ -403,6 +409,7 @@ __global__ void __launch_bounds__(D32_THREADS, 6) design32(D32Params P) {
     if (P.selected)
       for (int i = tid; i < ld; i += blockDim.x)
         P.selected[loc * ld + i] = (i < L.j) ? cl[L.sel[i]] : -1;
+    if (tid == 0) promote_location(P.promote, P.promote_count, loc, d32_vmin);
   }
 }
 
@@ -422,6 +429,8 @@ cudaError_t launch_exh32(const DesignArgs& a, cudaStream_t s) {
   P.selected = a.selected; P.tie_gap = a.tie_gap; P.nevals = a.nevals; P.Linv = a.ws->state64;
   P.Kc = a.ws->state32; P.crow = a.ws->crow; P.status = a.ws->status;
   P.queue = a.ws->queue + 2; P.order = a.order; P.count = a.count;
+  P.promote = a.promote ? a.ws->promote : nullptr;
+  P.promote_count = a.ws->status + 1;
   size_t sm = smem_design32(a.n_max, a.p, a.PP, a.nc_max);
   cudaError_t err =
       cudaFuncSetAttribute(design32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -50,8 +50,11 @@ struct D64Params {
   int32_t* selected;
   double* tie_gap;
   int32_t* nevals;
-  double* Kc;          // exhaustive correlation cache [M][n_max][nc_max]
+  double* Kc;          // exhaustive correlation cache [M][n_max][nc_max], or per CTA
+                       // [grid][n_max][nc_max] when the locations come from a list
   unsigned* status;
+  const int32_t* list; // locations to solve (list[0 .. *count - 1]), or null: CTA b solves b
+  const unsigned* count;
   int full;            // ray snaps over all of X_N through the k-d tree
   KdView<double> kd;   // the tree in binary64 (full scope)
 };
@@ -526,16 +529,15 @@ __device__ void predict(const D64Params& P, Loc& L, const int32_t* cl, double* m
 
 __device__ __forceinline__ size_t align8(size_t x) { return (x + 7) & ~(size_t)7; }
 
+// One location by the whole CTA (all threads call it); Kc_loc: the CTA's
+// correlation cache (exhaustive search).
 template <int SEARCH>
-__global__ void __launch_bounds__(D64_THREADS) design64(D64Params P) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int64_t loc = blockIdx.x;
-  if (loc >= P.M) return;
+__device__ void design64_location(const D64Params& P, const int64_t loc, double* Kc_loc,
+                                  unsigned char* smem) {
   const int tid = threadIdx.x, p = P.p, ld = P.n_max, R = P.R;
   const int nc = P.nc_loc ? P.nc_loc[loc] : P.nc_max;
   const int n = P.n_loc ? P.n_loc[loc] : P.n_max;
   const int32_t* cl = P.cand + loc * P.nc_max;
-  double* Kc_loc = (SEARCH == SEARCH_EXHAUSTIVE) ? P.Kc + loc * (int64_t)ld * P.nc_max : nullptr;
 
   Loc L;
   double* dp = reinterpret_cast<double*>(smem);
@@ -611,6 +613,27 @@ __global__ void __launch_bounds__(D64_THREADS) design64(D64Params P) {
   if (P.selected)
     for (int i = tid; i < ld; i += blockDim.x)
       P.selected[loc * ld + i] = (i < L.j) ? L.gsel[i] : -1;
+  __syncthreads();
+}
+
+// Without a list, CTA b solves location b.  With a list (the locations an
+// FP32 form hands over for a binary64 re-solve), the CTAs stride over its
+// *count entries, each with its own slot of the exhaustive cache.
+template <int SEARCH>
+__global__ void __launch_bounds__(D64_THREADS) design64(D64Params P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int64_t ldc = (int64_t)P.n_max * P.nc_max;
+  if (!P.list) {
+    const int64_t loc = blockIdx.x;
+    if (loc >= P.M) return;
+    design64_location<SEARCH>(P, loc, SEARCH == SEARCH_EXHAUSTIVE ? P.Kc + loc * ldc : nullptr,
+                              smem);
+    return;
+  }
+  const unsigned items = *P.count;
+  double* Kc_slot = SEARCH == SEARCH_EXHAUSTIVE ? P.Kc + (int64_t)blockIdx.x * ldc : nullptr;
+  for (unsigned it = blockIdx.x; it < items; it += gridDim.x)
+    design64_location<SEARCH>(P, (int64_t)P.list[it], Kc_slot, smem);
 }
 
 static size_t smem_design64(int n_max, int p, int nc_max, int R) {
@@ -621,13 +644,16 @@ static size_t smem_design64(int n_max, int p, int nc_max, int R) {
   return d * 8 + i * 4 + nc_max + 16;
 }
 
-cudaError_t launch_design_fp64(const DesignArgs& a, int search, cudaStream_t s) {
+cudaError_t launch_design_fp64(const DesignArgs& a, int search, cudaStream_t s,
+                               const int32_t* list, const unsigned* count, double* kc_slots,
+                               int grid_cap) {
   D64Params P;
   P.X = a.X; P.Y = a.Y; P.p = a.p; P.xref = a.xref; P.M = a.M; P.cand = a.cand;
   P.nc_max = a.nc_max; P.nc_loc = a.nc_loc; P.n0 = a.n0; P.n_max = a.n_max; P.n_loc = a.n_loc;
   P.theta = a.theta; P.theta_loc = a.theta_loc; P.g = a.g; P.R = a.nrays; P.lo = a.ws->lo; P.hi = a.ws->hi;
   P.mean = a.mean; P.s2 = a.s2; P.selected = a.selected; P.tie_gap = a.tie_gap;
-  P.nevals = a.nevals; P.Kc = a.ws->state64; P.status = a.ws->status;
+  P.nevals = a.nevals; P.Kc = list ? kc_slots : a.ws->state64; P.status = a.ws->status;
+  P.list = list; P.count = count;
   P.full = a.full_scope;
   if (P.full) {
     const KdTree& t = a.ws->kd;
@@ -637,20 +663,22 @@ cudaError_t launch_design_fp64(const DesignArgs& a, int search, cudaStream_t s) 
     std::memset(&P.kd, 0, sizeof(P.kd));
   }
   size_t sm = smem_design64(a.n_max, a.p, a.nc_max, a.nrays);
+  const int64_t grid = list ? (a.M < grid_cap ? a.M : grid_cap) : a.M;
+  if (grid <= 0) return cudaSuccess;
   cudaError_t err;
   if (search == SEARCH_EXHAUSTIVE) {
     err = cudaFuncSetAttribute(design64<SEARCH_EXHAUSTIVE>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (err != cudaSuccess) return err;
     prof_begin("design64_exhaustive", s);
-    design64<SEARCH_EXHAUSTIVE><<<(unsigned)a.M, D64_THREADS, sm, s>>>(P);
+    design64<SEARCH_EXHAUSTIVE><<<(unsigned)grid, D64_THREADS, sm, s>>>(P);
     prof_end(s);
   } else {
     err = cudaFuncSetAttribute(design64<SEARCH_RAY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)sm);
     if (err != cudaSuccess) return err;
     prof_begin("design64_ray", s);
-    design64<SEARCH_RAY><<<(unsigned)a.M, D64_THREADS, sm, s>>>(P);
+    design64<SEARCH_RAY><<<(unsigned)grid, D64_THREADS, sm, s>>>(P);
     prof_end(s);
   }
   return cudaGetLastError();

@@ -65,6 +65,8 @@ struct XtParams {
   unsigned* queue;       // work counter (zero at launch)
   const int32_t* order;  // item -> location, or null
   const unsigned* count; // items (device), or null (M)
+  int32_t* promote;      // binary64 re-solve list, or null (promotion off)
+  unsigned* promote_count;
 };
 
 #define XT_TILE_FLOATS (128 * XT_KMAX)   // one of hi / lo of a 128-candidate tile
@@ -263,6 +265,7 @@ __global__ void __launch_bounds__(XT_THREADS, 2) exh_tc_kernel(XtParams P) {
 
     int j = 0;
     bool ok = (n >= P.n0) && (n <= nc) && (n <= ld);
+    double vmin = INFINITY;   // smallest binary64 pivot of the local design (thread 0)
 
     // ---- append candidate rank rr: FP64 factor row, z, L^{-1}y, B row, Kc row ----
     auto add_point = [&](int rr) -> bool {
@@ -293,6 +296,7 @@ __global__ void __launch_bounds__(XT_THREADS, 2) exh_tc_kernel(XtParams P) {
       if (tid == 0) {
         const double v = (1.0 + P.g) - vv;
         red[0] = v;
+        if (P.promote) vmin = v > 0.0 ? fmin(vmin, v) : -1.0;
         red[1] = v > 0.0 ? 1.0 / sqrt(v) : 0.0;
       }
       __syncthreads();
@@ -482,6 +486,7 @@ __global__ void __launch_bounds__(XT_THREADS, 2) exh_tc_kernel(XtParams P) {
     }
     if (P.selected)
       for (int i = tid; i < ldo; i += XT_THREADS) P.selected[loc * ldo + i] = (i < j) ? cl[sel[i]] : -1;
+    if (tid == 0) promote_location(P.promote, P.promote_count, loc, vmin);
   }
   // after a timeout: wait (bounded) for the copy or MMAs still in flight
   if (a_pending) mbar_wait(bar_a, phase_a);
@@ -507,6 +512,8 @@ cudaError_t launch_exh_tc(const DesignArgs& a, cudaStream_t s) {
   P.Linv = a.ws->state64; P.Kc = a.ws->state32; P.status = a.ws->status;
   P.queue = a.ws->queue + 1; P.order = a.order; P.count = a.count;
   P.crow = a.ws->crow;
+  P.promote = a.promote ? a.ws->promote : nullptr;
+  P.promote_count = a.ws->status + 1;
   const size_t small = (size_t)((a.nc_max + 3) & ~3) * 4 + XT_KMAX * 4 + (size_t)XT_KMAX * a.p * 8 +
                        6 * XT_KMAX * 8 + 8 * 8 + 8 * 4 + 8 * 4 + XT_KMAX * 4 + a.nc_max + 96;
   const size_t sm = 1024 + XtSmem::END + small;

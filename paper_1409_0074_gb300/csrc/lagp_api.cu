@@ -71,6 +71,12 @@ size_t layout_request(const Shape& sh, void* base, Workspace* ws) {
   w->order_hist = static_cast<unsigned*>(c.take(512 * sizeof(unsigned)));
   w->order_count = static_cast<unsigned*>(c.take(2 * sizeof(unsigned)));
   w->order_key = static_cast<uint16_t*>(c.take(sizeof(uint16_t) * ch));
+  // precision promotion: the re-solve list and, for exhaustive search, the
+  // binary64 correlation cache of its CTAs
+  w->promote = static_cast<int32_t*>(c.take(sh.promote ? sizeof(int32_t) * ch : 0));
+  const int64_t pslots = ch < PROMOTE_SLOTS ? ch : PROMOTE_SLOTS;
+  w->promote64 = static_cast<double*>(c.take(sh.promote && sh.search == LAGP_EXHAUSTIVE
+      ? sizeof(double) * pslots * sh.n_max * sh.nc_max : 0));
   w->chunk = ch;
   return c.off;
 }
@@ -111,7 +117,9 @@ bool make_shape(int64_t N, int p, int64_t M, int n0, int n, int N_close, int nra
   if (n0 < 1 || n0 > n || n > LAGP_MAX_N || n > N_close || N_close > N || N_close > 4096)
     return false;
   if (search != LAGP_EXHAUSTIVE && search != LAGP_RAY && search != LAGP_RAY_FULL) return false;
-  if (precision != LAGP_FP64 && precision != LAGP_FP32_SCORE && precision != LAGP_FP32_SCORE_TC)
+  const int form = precision & ~LAGP_PROMOTE;
+  if (form != LAGP_FP32_SCORE && form != LAGP_FP32_SCORE_TC &&
+      (form != LAGP_FP64 || precision != LAGP_FP64))
     return false;
   if (N > (int64_t)0x7fffff00) return false;   // int32 design indices
   int R = nrays <= 0 ? p : nrays;
@@ -127,8 +135,9 @@ bool make_shape(int64_t N, int p, int64_t M, int n0, int n, int N_close, int nra
   sh->nc_max = N_close;
   sh->nrays = (search != LAGP_EXHAUSTIVE) ? R : 1;
   sh->search = search;
-  sh->precision = precision;
-  sh->chunk = chunk_for(M, search, precision, N_close, N);
+  sh->precision = form;
+  sh->promote = (precision & LAGP_PROMOTE) != 0;
+  sh->chunk = chunk_for(M, search, form, N_close, N);
   return true;
 }
 
@@ -145,10 +154,9 @@ extern "C" size_t laGP_workspace_bytes(int64_t N, int p, int64_t M, int n, int N
 
 namespace lagp {
 
-// Greedy design + prediction of one chunk whose candidates are in ws.cand.
-static cudaError_t run_design(const DesignArgs& a0, int search, int precision, bool uneven,
-                              cudaStream_t s) {
-  if (precision == LAGP_FP64) return launch_design_fp64(a0, search, s);
+// FP32-scoring greedy design + prediction of one chunk.
+static cudaError_t run_design32(const DesignArgs& a0, int search, int precision, bool uneven,
+                                cudaStream_t s) {
   const Workspace& ws = *a0.ws;
   DesignArgs a = a0;
   a.order = nullptr;
@@ -187,6 +195,24 @@ static cudaError_t run_design(const DesignArgs& a0, int search, int precision, b
   return launch_exh32(b, s);
 }
 
+// Greedy design + prediction of one chunk whose candidates are in ws.cand.
+// With LAGP_PROMOTE the FP32 forms list the locations whose smallest binary64
+// pivot fell below LAGP_PROMOTE_PIVOT, and the binary64 kernels then solve
+// those again (the count stays on the device: no host synchronisation).
+static cudaError_t run_design(const DesignArgs& a0, int search, int precision, bool uneven,
+                              cudaStream_t s) {
+  if (precision == LAGP_FP64) return launch_design_fp64(a0, search, s);
+  const Workspace& ws = *a0.ws;
+  cudaError_t e;
+  if (a0.promote && (e = cudaMemsetAsync(ws.status + 1, 0, sizeof(unsigned), s)) != cudaSuccess)
+    return e;
+  if ((e = run_design32(a0, search, precision, uneven, s)) != cudaSuccess || !a0.promote) return e;
+  DesignArgs b = a0;
+  b.order = nullptr;
+  b.count = nullptr;
+  return launch_design_fp64(b, search, s, ws.promote, ws.status + 1, ws.promote64, PROMOTE_SLOTS);
+}
+
 static DesignArgs chunk_args(const Shape& sh, const Call& c, const Workspace& ws, int64_t c0,
                              int64_t Mc, const Tune& t) {
   DesignArgs a;
@@ -202,13 +228,14 @@ static DesignArgs chunk_args(const Shape& sh, const Call& c, const Workspace& ws
   a.tie_gap = c.tie_gap ? c.tie_gap + c0 * n : nullptr;
   a.nevals = c.nevals ? c.nevals + c0 * n : nullptr;
   a.ws = &ws; a.order = nullptr; a.count = nullptr; a.tune = t;
+  a.promote = sh.promote;
   return a;
 }
 
 // The whole path on the stream: prepare, then per chunk kNN and design.
 int enqueue(const Shape& sh, const Call& c, const Workspace& ws, const Tune& t, cudaStream_t s,
             bool prepared) {
-  if (cudaMemsetAsync(ws.status, 0, sizeof(unsigned), s) != cudaSuccess) return LAGP_ERR_CUDA;
+  if (cudaMemsetAsync(ws.status, 0, 3 * sizeof(unsigned), s) != cudaSuccess) return LAGP_ERR_CUDA;
   if (!prepared && launch_prepare(c.design, sh.N, sh.p, sh.PP, sh.Npad, ws, s) != cudaSuccess)
     return LAGP_ERR_CUDA;
   const bool uneven = c.n_loc || c.nclose_loc;
@@ -274,7 +301,7 @@ extern "C" int laGP_autotune(const double* design, const double* y, int64_t N, i
   if (!choice) return LAGP_ERR_INVALID;
   const bool uneven = n_loc || nclose_loc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (precision == LAGP_FP64) {   // the FP64 kernels have no launch choices
+  if (sh.precision == LAGP_FP64) {   // the FP64 kernels have no launch choices
     *choice = encode_tune(default_tune());
     return LAGP_OK;
   }
@@ -292,7 +319,7 @@ extern "C" int laGP_autotune(const double* design, const double* y, int64_t N, i
   // kNN of the first chunk once; then each candidate's design launch, timed
   const Call c{design, y, xref, theta, g, n_loc, nclose_loc, mean, s2, nullptr, nullptr, nullptr};
   const int64_t Mc = sh.M < sh.chunk ? sh.M : sh.chunk;
-  if (cudaMemsetAsync(ws.status, 0, sizeof(unsigned), s) != cudaSuccess) return LAGP_ERR_CUDA;
+  if (cudaMemsetAsync(ws.status, 0, 3 * sizeof(unsigned), s) != cudaSuccess) return LAGP_ERR_CUDA;
   if (launch_prepare(design, sh.N, sh.p, sh.PP, sh.Npad, ws, s) != cudaSuccess) return LAGP_ERR_CUDA;
   if (launch_knn(design, sh.N, sh.p, sh.PP, sh.Npad, xref, Mc, sh.nc_max, nclose_loc, ws.cand, ws,
                  s) != cudaSuccess)
@@ -306,9 +333,9 @@ extern "C" int laGP_autotune(const double* design, const double* y, int64_t N, i
   for (int i = 0; i < nc && out == LAGP_OK; ++i) {
     const DesignArgs a = chunk_args(sh, c, ws, 0, Mc, cand[i]);
     float ms = 0.f;
-    if (run_design(a, search, precision, uneven, s) != cudaSuccess ||    // warm-up
+    if (run_design(a, search, sh.precision, uneven, s) != cudaSuccess ||    // warm-up
         cudaEventRecord(e0, s) != cudaSuccess ||
-        run_design(a, search, precision, uneven, s) != cudaSuccess ||
+        run_design(a, search, sh.precision, uneven, s) != cudaSuccess ||
         cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
         cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
       out = LAGP_ERR_CUDA;
@@ -365,7 +392,7 @@ extern "C" int laGP_knn(const double* design, int64_t N, int p, const double* xr
   const size_t need = layout_workspace(sh, workspace, &ws);
   if (workspace_bytes < need) return LAGP_ERR_WORKSPACE;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (cudaMemsetAsync(ws.status, 0, sizeof(unsigned), s) != cudaSuccess) return LAGP_ERR_CUDA;
+  if (cudaMemsetAsync(ws.status, 0, 3 * sizeof(unsigned), s) != cudaSuccess) return LAGP_ERR_CUDA;
   if (launch_prepare(design, N, p, sh.PP, sh.Npad, ws, s) != cudaSuccess) return LAGP_ERR_CUDA;
   for (int64_t c0 = 0; c0 < M; c0 += sh.chunk) {
     const int64_t Mc = (M - c0 < sh.chunk) ? M - c0 : sh.chunk;
@@ -387,6 +414,19 @@ extern "C" int laGP_status(void* workspace, void* stream, unsigned* status) {
   if (cudaMemsetAsync(dev, 0, sizeof(unsigned), s) != cudaSuccess) return LAGP_ERR_CUDA;
   *status = host;
   return host ? LAGP_ERR_DEVICE : LAGP_OK;
+}
+
+extern "C" int laGP_promoted(void* workspace, void* stream, int64_t* count) {
+  if (!workspace || !count) return LAGP_ERR_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned host = 0;
+  // status word 2 totals the promoted locations of the call
+  const unsigned* dev = static_cast<const unsigned*>(workspace) + 2;
+  if (cudaMemcpyAsync(&host, dev, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return LAGP_ERR_CUDA;
+  *count = host;
+  return LAGP_OK;
 }
 
 // Host form: [design | y | xref | n_loc | nclose_loc | mean | s2 | selected | tie_gap |
@@ -497,7 +537,7 @@ extern "C" int laGP_build_and_predict_mle(const double* design, const double* y,
   if (workspace_bytes < base + align256(sizeof(int32_t) * sh.chunk * n)) return LAGP_ERR_WORKSPACE;
   int32_t* selbuf = reinterpret_cast<int32_t*>(static_cast<char*>(workspace) + base);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (cudaMemsetAsync(ws.status, 0, sizeof(unsigned), s) != cudaSuccess) return LAGP_ERR_CUDA;
+  if (cudaMemsetAsync(ws.status, 0, 3 * sizeof(unsigned), s) != cudaSuccess) return LAGP_ERR_CUDA;
   if (launch_prepare(design, sh.N, sh.p, sh.PP, sh.Npad, ws, s) != cudaSuccess)
     return LAGP_ERR_CUDA;
   const Tune t = tune_for(sh, false);

@@ -37,8 +37,15 @@ struct Workspace {
   unsigned* order_count;// [2] items per part
   uint16_t* order_key;  // [chunk] part and cost bucket
   KdTree kd;            // k-d tree over the design (LAGP_RAY_FULL; kd.perm null otherwise)
+  int32_t* promote;     // [chunk] locations handed to the binary64 re-solve (LAGP_PROMOTE);
+                        // status[1] counts them per launch, status[2] per call
+  double* promote64;    // exhaustive re-solve: [PROMOTE_SLOTS][n_max][nc_max] FP64 cache
   int64_t chunk;
 };
+
+// CTAs of the binary64 re-solve of promoted locations (each with its own slot
+// of the exhaustive correlation cache).
+#define PROMOTE_SLOTS 608
 
 // Warp slots of the persistent ray kernel and CTA slots of the persistent
 // exhaustive kernels: their FP64 / correlation scratch is per slot, so a
@@ -100,7 +107,8 @@ struct Shape {
   int64_t Npad;
   int64_t M;
   int n0, n_max, nc_max, nrays;
-  int search, precision;
+  int search, precision;      // precision: the form, LAGP_PROMOTE stripped
+  bool promote;               // FP32 forms with LAGP_PROMOTE
   int64_t chunk;
 };
 
@@ -151,6 +159,7 @@ struct DesignArgs {
   const Workspace* ws;
   const int32_t* order;    // work order of the launch (device) or null
   const unsigned* count;   // items in `order` (device) or null
+  bool promote;            // FP32 forms: list ill-conditioned locations in ws->promote
   Tune tune;
 };
 
@@ -193,7 +202,13 @@ void prof_begin(const char* name, cudaStream_t s);
 void prof_end(cudaStream_t s);
 void prof_suspend(bool on);
 
-cudaError_t launch_design_fp64(const DesignArgs& a, int search, cudaStream_t s);
+// Binary64 greedy design and prediction (design_fp64.cu): every location of
+// the chunk, or with `list` the *count locations list[0 ..] (device count) on
+// at most grid_cap CTAs, each with its slot of kc_slots for the exhaustive
+// correlation cache.
+cudaError_t launch_design_fp64(const DesignArgs& a, int search, cudaStream_t s,
+                               const int32_t* list = nullptr, const unsigned* count = nullptr,
+                               double* kc_slots = nullptr, int grid_cap = 0);
 // Local maximum-likelihood lengthscale on the designs sel [M][n] and the
 // predictive equations at it (mle.cu); the start is theta0_loc[m] when given.
 bool mle_shape_ok(int p, int n);

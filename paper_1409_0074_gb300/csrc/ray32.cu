@@ -65,6 +65,8 @@ struct RayParams {
   const unsigned* count;// number of items (device), or null (M)
   int full;             // snap over all of X_N through the k-d tree
   KdView<float> kd;     // the tree in centred FP32 coordinates (full scope)
+  int32_t* promote;     // binary64 re-solve list, or null (promotion off)
+  unsigned* promote_count;
 };
 
 // start of row i in the zero-padded FP32 row storage (rows of length
@@ -83,7 +85,7 @@ __device__ __host__ __forceinline__ int kz_ld(int n) {
 }
 
 struct WarpLayout {
-  int lf, kz, zf, sf, ae, x, sel, gsel, stk, bnd, starts, mask, smask, bytes;
+  int lf, kz, zf, sf, ae, x, sel, gsel, stk, bnd, starts, mask, smask, vm, bytes;
 };
 
 __host__ __device__ inline WarpLayout warp_layout(int n, int PP, int RP, int nc) {
@@ -103,6 +105,7 @@ __host__ __device__ inline WarpLayout warp_layout(int n, int PP, int RP, int nc)
   w.starts = take(RP);
   w.mask = take((nc + 31) / 32);
   w.smask = take((nc + 31) / 32);
+  w.vm = take(2);              // smallest binary64 pivot of the location (lane 0)
   w.bytes = off * 4;
   return w;
 }
@@ -201,6 +204,7 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
   int* starts = reinterpret_cast<int*>(base + lay.starts);
   uint32_t* mask = reinterpret_cast<uint32_t*>(base + lay.mask);     // selected candidates
   uint32_t* smask = reinterpret_cast<uint32_t*>(base + lay.smask);   // this step's ray starts
+  double* vmin = reinterpret_cast<double*>(base + lay.vm);
   const int KP = kz_ld(ldn);
 
   double* kx64 = Lg + tri(ldn);
@@ -230,6 +234,7 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
 
   int j = 0;
   bool ok = (n >= P.n0) && (n <= nc) && (n <= ldn);
+  if (lane == 0) *vmin = INFINITY;
 
   // ---- append design point gi (candidate rank rr, or -1) (FP64 factor row) ----
   auto add_point = [&](int gi, int rr) -> bool {
@@ -257,6 +262,7 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
     lzy = warp_sum64(lzy);
     __syncwarp();
     const double v = (1.0 + P.g) - vv;
+    if (lane == 0) *vmin = v > 0.0 ? fmin(*vmin, v) : -1.0;
     if (!(v > 0.0)) return false;
     const double inv_d = rsqrt(v);
     double* Lj = Lg + tri(j);
@@ -587,6 +593,7 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
   }
   if (P.selected)
     for (int i = lane; i < ldn; i += 32) P.selected[loc * ldn + i] = (i < j) ? gsel[i] : -1;
+  if (lane == 0) promote_location(P.promote, P.promote_count, loc, *vmin);
 }
 
 // at least 20 resident warps per SM (at most 102 registers per thread)
@@ -641,6 +648,8 @@ cudaError_t launch_ray32(const DesignArgs& a, cudaStream_t s) {
   P.g64_stride = (int64_t)ray32_g64_doubles(a.n_max); P.status = a.ws->status;
   P.queue = a.ws->queue; P.order = a.order; P.count = a.count;
   P.full = a.full_scope;
+  P.promote = a.promote ? a.ws->promote : nullptr;
+  P.promote_count = a.ws->status + 1;
   if (P.full) {
     const KdTree& t = a.ws->kd;
     P.kd.box = t.box32; P.kd.stride = a.PP; P.kd.p = a.p; P.kd.D = t.D; P.kd.N = a.N;

@@ -15,8 +15,13 @@ LIB_PATH = os.path.join(HERE, "liblagp_gb300.so")
 
 LAGP_EXHAUSTIVE, LAGP_RAY, LAGP_RAY_FULL = 0, 1, 2
 LAGP_FP64, LAGP_FP32_SCORE, LAGP_FP32_SCORE_TC = 0, 1, 2
+LAGP_PROMOTE = 16
+LAGP_PROMOTE_PIVOT = 3e-5
 SEARCH = {"exhaustive": LAGP_EXHAUSTIVE, "ray": LAGP_RAY, "ray_full": LAGP_RAY_FULL}
-PRECISION = {"fp64": LAGP_FP64, "fp32": LAGP_FP32_SCORE, "fp32_tc": LAGP_FP32_SCORE_TC}
+# "_promote": the FP32 form re-solves its ill-conditioned locations in binary64
+PRECISION = {"fp64": LAGP_FP64, "fp32": LAGP_FP32_SCORE, "fp32_tc": LAGP_FP32_SCORE_TC,
+             "fp32_promote": LAGP_FP32_SCORE | LAGP_PROMOTE,
+             "fp32_tc_promote": LAGP_FP32_SCORE_TC | LAGP_PROMOTE}
 ERRORS = {-1: "invalid argument", -2: "workspace too small", -3: "CUDA error",
           -4: "device reported a failure"}
 STATUS_BITS = {1: "timeout", 2: "kNN tie capacity", 4: "numeric (v <= 0)"}
@@ -30,7 +35,8 @@ EXPORTED = ("laGP_workspace_bytes", "laGP_build_and_predict", "laGP_knn_workspac
             "laGP_plan_launch", "laGP_plan_destroy", "laGP_ctx_design_bytes",
             "laGP_ctx_request_bytes", "laGP_ctx_create", "laGP_ctx_submit", "laGP_ctx_poll",
             "laGP_ctx_wait", "laGP_ctx_capacity", "laGP_ctx_destroy", "laGP_mle_predict",
-            "laGP_mle_workspace_bytes", "laGP_build_and_predict_mle")
+            "laGP_mle_workspace_bytes", "laGP_build_and_predict_mle", "laGP_promoted",
+            "laGP_sep_mle_workspace_bytes", "laGP_sep_mle", "laGP_prescale")
 
 _lib = None
 
@@ -69,6 +75,8 @@ def load():
     lib.laGP_knn.argtypes = [vp, i64, i32, vp, i64, i32, vp, vp, sz, vp]
     lib.laGP_status.restype = i32
     lib.laGP_status.argtypes = [vp, vp, C.POINTER(C.c_uint)]
+    lib.laGP_promoted.restype = i32
+    lib.laGP_promoted.argtypes = [vp, vp, C.POINTER(C.c_int64)]
     lib.laGP_profile.restype = i32
     lib.laGP_profile.argtypes = [i32]
     lib.laGP_profile_read.restype = i32
@@ -114,6 +122,13 @@ def load():
     lib.laGP_mle_predict.restype = i32
     lib.laGP_mle_predict.argtypes = [vp, vp, i64, i32, vp, i64, vp, i32, dbl, dbl, dbl, dbl,
                                      vp, vp, vp, vp, vp, vp]
+    lib.laGP_sep_mle_workspace_bytes.restype = sz
+    lib.laGP_sep_mle_workspace_bytes.argtypes = [i32, i32]
+    lib.laGP_sep_mle.restype = i32
+    lib.laGP_sep_mle.argtypes = [vp, vp, i64, i32, vp, i32, dbl, dbl, dbl, dbl, i32, vp, vp, vp,
+                                 sz, vp]
+    lib.laGP_prescale.restype = i32
+    lib.laGP_prescale.argtypes = [vp, i64, i32, vp, vp, vp]
     _lib = lib
     return lib
 
@@ -211,6 +226,59 @@ def laGP_mle_predict(design, y, xref, sel, theta0, g, tmin, tmax, theta_out, mea
     _check("laGP_mle_predict", rc)
 
 
+def laGP_sep_mle_workspace_bytes(n_sub, p):
+    return load().laGP_sep_mle_workspace_bytes(n_sub, p)
+
+
+def laGP_sep_mle(design, y, subset, g, theta0, tmin, tmax, maxit, theta_out, workspace,
+                 info=None, stream=None):
+    """Separable global lengthscales on the design rows `subset` (blocks until
+    the fit ends)."""
+    import torch
+    N, p = design.shape
+    n = subset.shape[0]
+    rc = load().laGP_sep_mle(_ptr(design, torch.float64), _ptr(y, torch.float64, N), N, p,
+                             _ptr(subset, torch.int32, n), n, float(g), float(theta0),
+                             float(tmin), float(tmax), int(maxit),
+                             _ptr(theta_out, torch.float64, p), _ptr(info, torch.int32, 3),
+                             _ptr(workspace), workspace.numel() * workspace.element_size(),
+                             _stream(stream))
+    _check("laGP_sep_mle", rc)
+
+
+def laGP_prescale(X, theta, X_out, stream=None):
+    import torch
+    rows, p = X.shape
+    _check("laGP_prescale", load().laGP_prescale(_ptr(X, torch.float64), rows, p,
+                                                 _ptr(theta, torch.float64, p),
+                                                 _ptr(X_out, torch.float64, rows * p),
+                                                 _stream(stream)))
+
+
+def sep_mle(design, y, subset, g, theta0, tmin, tmax, maxit=200, stream=None):
+    """Convenience wrapper of laGP_sep_mle: returns (theta [p] CUDA tensor,
+    (iterations, evaluations, status))."""
+    import torch
+    p = design.shape[1]
+    wsb = laGP_sep_mle_workspace_bytes(subset.shape[0], p)
+    if wsb == 0:
+        raise LagpError("laGP_sep_mle_workspace_bytes", -1)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=design.device)
+    th = torch.empty(p, dtype=torch.float64, device=design.device)
+    info = torch.zeros(3, dtype=torch.int32, device=design.device)
+    laGP_sep_mle(design, y, subset, g, theta0, tmin, tmax, maxit, th, ws, info=info,
+                 stream=stream)
+    return th, tuple(int(v) for v in info.cpu())
+
+
+def prescale(X, theta, stream=None):
+    """X / sqrt(theta) as a new CUDA tensor."""
+    import torch
+    out = torch.empty_like(X)
+    laGP_prescale(X, theta, out, stream=stream)
+    return out
+
+
 def mle_predict(design, y, xref, sel, theta0, g, tmin, tmax, stream=None):
     """Convenience wrapper: allocates the outputs, runs laGP_mle_predict and
     checks the device status.  Returns a dict of CUDA tensors (theta, mean, s2,
@@ -254,9 +322,11 @@ def laGP_build_and_predict_mle(design, y, xref, n0, n, N_close, theta0, g, tmin,
 
 
 def predict_mle(design, y, xref, n0, n, N_close, theta0, g, tmin, tmax, stages=1,
-                search="ray", nrays=0, precision="fp64", want_selected=False, stream=None):
+                search="ray", nrays=0, precision="fp64", want_selected=False,
+                want_promoted=False, stream=None):
     """Convenience wrapper of laGP_build_and_predict_mle: allocates outputs and
-    workspace, checks the device status; returns a dict of CUDA tensors."""
+    workspace, checks the device status; returns a dict of CUDA tensors (and,
+    with want_promoted, the int "promoted")."""
     import torch
     dev = design.device
     M = xref.shape[0]
@@ -275,6 +345,8 @@ def predict_mle(design, y, xref, n0, n, N_close, theta0, g, tmin, tmax, stages=1
     rc, st = laGP_status(ws, stream)
     if rc != 0:
         raise LagpError("laGP_build_and_predict_mle (device)", rc, st)
+    if want_promoted:
+        out["promoted"] = laGP_promoted(ws, stream)
     return out
 
 
@@ -282,6 +354,13 @@ def laGP_status(workspace, stream=None):
     st = C.c_uint(0)
     rc = load().laGP_status(_ptr(workspace), _stream(stream), C.byref(st))
     return rc, st.value
+
+
+def laGP_promoted(workspace, stream=None):
+    """Locations the last call on this workspace re-solved in binary64."""
+    cnt = C.c_int64(0)
+    _check("laGP_promoted", load().laGP_promoted(_ptr(workspace), _stream(stream), C.byref(cnt)))
+    return cnt.value
 
 
 def laGP_profile(enable):
@@ -321,9 +400,10 @@ def laGP_build_and_predict_host(design, y, xref, n0, n, N_close, theta, g, searc
 
 
 def predict(design, y, xref, n0, n, N_close, theta, g, search="ray", nrays=0, precision="fp32",
-            n_loc=None, nclose_loc=None, want_trace=False, stream=None):
+            n_loc=None, nclose_loc=None, want_trace=False, want_promoted=False, stream=None):
     """Convenience wrapper: allocates outputs and workspace with torch, enqueues
-    the path, checks the device status.  Returns a dict of CUDA tensors."""
+    the path, checks the device status.  Returns a dict of CUDA tensors (and,
+    with want_promoted, the int "promoted": locations re-solved in binary64)."""
     import torch
     dev = design.device
     M = xref.shape[0]
@@ -346,6 +426,8 @@ def predict(design, y, xref, n0, n, N_close, theta, g, search="ray", nrays=0, pr
     rc, st = laGP_status(ws, stream)
     if rc != 0:
         raise LagpError("laGP_build_and_predict (device)", rc, st)
+    if want_promoted:
+        out["promoted"] = laGP_promoted(ws, stream)
     return out
 
 

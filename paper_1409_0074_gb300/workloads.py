@@ -156,3 +156,10 @@ def small(N=600, p=2, M=8, n0=4, n=12, nc=60, theta=0.05, g=1e-6, seed=0, search
     return generate(Workload("small_%dd_N%d" % (p, N), N=N, p=p, M=M, n0=n0, n=n, nc=nc,
                              theta=theta, g=g, search=search, nrays=nrays, response=response,
                              seed=seed))
+
+
+def subset(N, n, seed=1):
+    """n distinct design rows drawn uniformly without replacement (the random
+    subset of the crude global analysis that pre-scales the inputs, Sec 5.3),
+    as int32 row indices in draw order."""
+    return np.random.default_rng(seed).permutation(N)[:n].astype(np.int32)

@@ -52,6 +52,9 @@ def test_workspace_sizes_and_argument_checks(lib):
         (100000, 4, 10, 50, 1000, 4, 3, 0),      # bad search
         (100000, 4, 10, 50, 1000, 4, 1, 3),      # bad precision
         (100000, 4, 10, 50, 1000, 4, 1, -1),     # bad precision
+        (100000, 4, 10, 50, 1000, 4, 1, 16),     # promotion of the FP64 form
+        (100000, 4, 10, 50, 1000, 4, 1, 3 | 16), # bad form with the promotion flag
+        (100000, 4, 10, 50, 1000, 4, 1, 32),     # unknown flag
     ]
     for args in bad:
         assert lagp.laGP_workspace_bytes(*args) == 0, args
@@ -60,6 +63,16 @@ def test_workspace_sizes_and_argument_checks(lib):
     f32 = [lagp.laGP_workspace_bytes(100000, 8, 10000, 50, 1000, 8, lagp.LAGP_EXHAUSTIVE, pr)
            for pr in (lagp.LAGP_FP32_SCORE, lagp.LAGP_FP32_SCORE_TC)]
     assert 0 < f32[0] < f32[1]
+    # LAGP_PROMOTE adds the re-solve list, and for exhaustive search the
+    # binary64 correlation cache of its 608 CTAs
+    for search in (lagp.LAGP_RAY, lagp.LAGP_EXHAUSTIVE):
+        off = lagp.laGP_workspace_bytes(100000, 8, 10000, 50, 1000, 8, search,
+                                        lagp.LAGP_FP32_SCORE)
+        on = lagp.laGP_workspace_bytes(100000, 8, 10000, 50, 1000, 8, search,
+                                       lagp.LAGP_FP32_SCORE | lagp.LAGP_PROMOTE)
+        assert 0 < off < on
+        if search == lagp.LAGP_EXHAUSTIVE:
+            assert on - off >= 8 * 608 * 50 * 1000
     assert lagp.laGP_knn_workspace_bytes(1000, 3, 10, 1) > 0
     assert lagp.laGP_host_workspace_bytes(1000, 3, 10, 10, 100, 2, 1, 1) > \
         lagp.laGP_workspace_bytes(1000, 3, 10, 10, 100, 2, 1, 1)
@@ -175,3 +188,39 @@ def test_mle_entry_argument_checks(lib):
     assert f(*common, 0.5, 1e-6, 1e-3, 2.0, 1, 1, 2, 0, p, p, p, None, p, small - 1, None) == -2
     m0 = (p, p, 1000, 2, p, 0, 6, 30, 100)
     assert f(*m0, 0.5, 1e-6, 1e-3, 2.0, 2, 1, 2, 0, None, None, None, None, None, 0, None) == 0
+
+
+def test_prescaling_argument_checks_return_before_touching_the_device(lib):
+    """laGP_sep_mle and laGP_prescale reject bad sizes and NULL pointers on the
+    host (the fake pointers below are never dereferenced)."""
+    from paper_1409_0074_gb300 import lagp
+    L = lagp.load()
+    assert L.laGP_sep_mle_workspace_bytes(1000, 8) >= 8 * 1000 * 1000
+    for n, p in ((1, 8), (1025, 8), (100, 0), (100, 17)):
+        assert L.laGP_sep_mle_workspace_bytes(n, p) == 0
+    fake = 4096
+    ws = L.laGP_sep_mle_workspace_bytes(100, 4)
+    good = [fake, fake, 1000, 4, fake, 100, 1e-6, 1.0, 1e-3, 10.0, 50, fake, None, fake, ws, None]
+    bad = [
+        dict(i=0, v=None),           # design NULL
+        dict(i=4, v=None),           # subset NULL
+        dict(i=11, v=None),          # theta_out NULL
+        dict(i=5, v=1),              # n_sub < 2
+        dict(i=5, v=2000),           # n_sub > 1024
+        dict(i=2, v=50),             # N < n_sub
+        dict(i=7, v=0.0),            # theta0 <= 0
+        dict(i=8, v=0.0),            # tmin <= 0
+        dict(i=9, v=1e-4),           # tmax < tmin
+        dict(i=10, v=0),             # maxit < 1
+        dict(i=6, v=-1.0),           # g < 0
+    ]
+    for b in bad:
+        a = list(good)
+        a[b["i"]] = b["v"]
+        assert L.laGP_sep_mle(*a) == -1, b
+    a = list(good)
+    a[14] = ws - 1
+    assert L.laGP_sep_mle(*a) == -2
+    assert L.laGP_prescale(fake, 10, 0, fake, fake, None) == -1
+    assert L.laGP_prescale(None, 10, 3, fake, fake, None) == -1
+    assert L.laGP_prescale(None, 0, 3, None, None, None) == 0
