@@ -94,10 +94,8 @@ struct L32 {
   float neg_inv_theta, onepg;
 };
 
-// lengthscale of the CTA's current location, and the smallest binary64 pivot
-// of its local design (kept out of the registers)
+// lengthscale of the CTA's current location (kept out of the registers)
 static __shared__ double d32_theta;
-static __shared__ double d32_vmin;
 
 __device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -208,7 +206,6 @@ __device__ bool add_point32(const D32Params& P, L32& L, const int32_t* cl, const
   if (tid == 0) {
     const double v = (1.0 + P.g) - vv;
     piv[0] = v;
-    if (P.promote) d32_vmin = v > 0.0 ? fmin(d32_vmin, v) : -1.0;
     piv[1] = v > 0.0 ? 1.0 / sqrt(v) : 0.0;
   }
   __syncthreads();
@@ -303,6 +300,9 @@ __device__ int search_exh32(const L32& L, int nc, double* gap_out) {
   return b.i;
 }
 
+// PROMOTE: with precision promotion (a separate instantiation, so that the
+// default one carries none of its code)
+template <bool PROMOTE>
 __global__ void __launch_bounds__(D32_THREADS, 6) design32(D32Params P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned s_item;
@@ -350,7 +350,6 @@ __global__ void __launch_bounds__(D32_THREADS, 6) design32(D32Params P) {
     const int n = P.n_loc ? P.n_loc[loc] : P.n_max;
     const int32_t* cl = P.cand + loc * P.nc_max;
     L.j = 0;
-    if (tid == 0) d32_vmin = INFINITY;
     if (P.theta_loc) {
       const double th = P.theta_loc[loc];
       if (tid == 0) d32_theta = th;
@@ -409,7 +408,16 @@ __global__ void __launch_bounds__(D32_THREADS, 6) design32(D32Params P) {
     if (P.selected)
       for (int i = tid; i < ld; i += blockDim.x)
         P.selected[loc * ld + i] = (i < L.j) ? cl[L.sel[i]] : -1;
-    if (tid == 0) promote_location(P.promote, P.promote_count, loc, d32_vmin);
+    if (PROMOTE && tid == 0) {
+      // smallest binary64 pivot v of the design: the factor's diagonal holds
+      // 1 / sqrt(v); a failed update promotes the location
+      double vm = ok ? INFINITY : -1.0;
+      for (int i = 0; i < L.j; ++i) {
+        const double dg = Lg[(int64_t)i * ld + i];
+        vm = fmin(vm, 1.0 / (dg * dg));
+      }
+      promote_location(P.promote, P.promote_count, loc, vm);
+    }
   }
 }
 
@@ -432,15 +440,15 @@ cudaError_t launch_exh32(const DesignArgs& a, cudaStream_t s) {
   P.promote = a.promote ? a.ws->promote : nullptr;
   P.promote_count = a.ws->status + 1;
   size_t sm = smem_design32(a.n_max, a.p, a.PP, a.nc_max);
-  cudaError_t err =
-      cudaFuncSetAttribute(design32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  auto k = P.promote ? design32<true> : design32<false>;
+  cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (err != cudaSuccess) return err;
-  const int64_t grid = persistent_grid(design32, D32_THREADS, sm, a.M, exh_slots(a.ws->chunk), 1,
+  const int64_t grid = persistent_grid(k, D32_THREADS, sm, a.M, exh_slots(a.ws->chunk), 1,
                                        a.tune.exh_occ);
   if (grid < 0) return cudaErrorInvalidValue;
   if ((err = cudaMemsetAsync(P.queue, 0, sizeof(unsigned), s)) != cudaSuccess) return err;
   prof_begin("design32_exhaustive", s);
-  design32<<<(unsigned)grid, D32_THREADS, sm, s>>>(P);
+  k<<<(unsigned)grid, D32_THREADS, sm, s>>>(P);
   prof_end(s);
   return cudaGetLastError();
 }

@@ -265,7 +265,6 @@ __global__ void __launch_bounds__(XT_THREADS, 2) exh_tc_kernel(XtParams P) {
 
     int j = 0;
     bool ok = (n >= P.n0) && (n <= nc) && (n <= ld);
-    double vmin = INFINITY;   // smallest binary64 pivot of the local design (thread 0)
 
     // ---- append candidate rank rr: FP64 factor row, z, L^{-1}y, B row, Kc row ----
     auto add_point = [&](int rr) -> bool {
@@ -296,7 +295,6 @@ __global__ void __launch_bounds__(XT_THREADS, 2) exh_tc_kernel(XtParams P) {
       if (tid == 0) {
         const double v = (1.0 + P.g) - vv;
         red[0] = v;
-        if (P.promote) vmin = v > 0.0 ? fmin(vmin, v) : -1.0;
         red[1] = v > 0.0 ? 1.0 / sqrt(v) : 0.0;
       }
       __syncthreads();
@@ -486,7 +484,16 @@ __global__ void __launch_bounds__(XT_THREADS, 2) exh_tc_kernel(XtParams P) {
     }
     if (P.selected)
       for (int i = tid; i < ldo; i += XT_THREADS) P.selected[loc * ldo + i] = (i < j) ? cl[sel[i]] : -1;
-    if (tid == 0) promote_location(P.promote, P.promote_count, loc, vmin);
+    if (P.promote && tid == 0) {
+      // smallest binary64 pivot v of the design: the factor's diagonal holds
+      // 1 / sqrt(v); a failed update promotes the location
+      double vm = ok ? INFINITY : -1.0;
+      for (int i = 0; i < j; ++i) {
+        const double dg = Lg[(int64_t)i * ld + i];
+        vm = fmin(vm, 1.0 / (dg * dg));
+      }
+      promote_location(P.promote, P.promote_count, loc, vm);
+    }
   }
   // after a timeout: wait (bounded) for the copy or MMAs still in flight
   if (a_pending) mbar_wait(bar_a, phase_a);

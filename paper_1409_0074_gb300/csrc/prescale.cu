@@ -13,8 +13,9 @@
 // One evaluation: the gathered subset rows -> K (n x n, binary64) -> K^{-1}
 // in place by Gauss-Jordan elimination without pivoting (K is symmetric
 // positive definite; the pivots are the successive Schur complements, so
-// their logs sum to log|K|), one launch per pivot with the pivot's row and
-// column double-buffered so that no launch reads what it writes -> alpha ->
+// their logs sum to log|K|), one launch per pivot with the pivot's row,
+// column and reciprocal double-buffered so that no launch reads what it
+// writes -> alpha ->
 // per-row partial sums of the trace and quadratic-form terms (one warp per
 // row, fixed order) -> the likelihood and its gradient in eta = log theta on
 // one thread, which also advances the maximiser.
@@ -57,7 +58,8 @@ struct SepWork {
   double* S;       // [n][p] subset rows
   double* ys;      // [n]
   double* A;       // [n][n] K, then K^{-1}
-  double* snap;    // [2][2][n] pivot column / row of the current and next step
+  double* snap;    // [2][2][n] pivot column / row of the current and next step, then
+                   // [2] the reciprocal pivot of the current and next step
   double* piv;     // [n]
   double* alpha;   // [n]
   double* part;    // [n][2p] per-row partial sums
@@ -77,7 +79,7 @@ static size_t sep_layout(int n, int p, char* base, SepWork* w) {
   t.S = reinterpret_cast<double*>(take(sizeof(double) * n * p));
   t.ys = reinterpret_cast<double*>(take(sizeof(double) * n));
   t.A = reinterpret_cast<double*>(take(sizeof(double) * n * n));
-  t.snap = reinterpret_cast<double*>(take(sizeof(double) * 4 * n));
+  t.snap = reinterpret_cast<double*>(take(sizeof(double) * (4 * n + 2)));
   t.piv = reinterpret_cast<double*>(take(sizeof(double) * n));
   t.alpha = reinterpret_cast<double*>(take(sizeof(double) * n));
   t.part = reinterpret_cast<double*>(take(sizeof(double) * n * 2 * p));
@@ -129,11 +131,14 @@ __global__ void sep_build(int n, int p, double g, SepWork w) {
   w.A[(int64_t)a * n + b] = v;
   if (b == 0) w.snap[a] = v;            // column 0
   if (a == 0) w.snap[n + b] = v;        // row 0
+  if (a == 0 && b == 0) w.snap[4 * n] = 1.0 / v;
 }
 
 // Gauss-Jordan step k: every element from its own value and the pivot's
-// column (cin) and row (rin) as they were before the step; the new column and
-// row k + 1 go to cout / rout for the next step.
+// column (cin) and row (rin) as they were before the step, with the pivot's
+// reciprocal computed once by the previous step; the new column and row
+// k + 1 go to cout / rout, and the thread that forms the next pivot also
+// forms its reciprocal, for the next step.
 __global__ void gj_step(int n, int k, SepWork w) {
   if (w.st->done) return;
   const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y * blockDim.y + threadIdx.y;
@@ -142,21 +147,22 @@ __global__ void gj_step(int n, int k, SepWork w) {
   const double* rin = cin + n;
   double* cout = w.snap + ((k + 1) & 1) * 2 * n;
   double* rout = cout + n;
-  const double pv = rin[k];
+  const double pi = w.snap[4 * n + (k & 1)];
   double v;
   if (i == k && j == k) {
-    v = 1.0 / pv;
-    w.piv[k] = pv;
+    v = pi;
+    w.piv[k] = rin[k];
   } else if (j == k) {
-    v = -cin[i] / pv;
+    v = -cin[i] * pi;
   } else if (i == k) {
-    v = rin[j] / pv;
+    v = rin[j] * pi;
   } else {
-    v = w.A[(int64_t)i * n + j] - cin[i] * rin[j] / pv;
+    v = fma(-cin[i] * pi, rin[j], w.A[(int64_t)i * n + j]);
   }
   w.A[(int64_t)i * n + j] = v;
   if (j == k + 1) cout[i] = v;
   if (i == k + 1) rout[j] = v;
+  if (i == k + 1 && j == k + 1) w.snap[4 * n + ((k + 1) & 1)] = 1.0 / v;
 }
 
 __device__ __forceinline__ double warp_sum_d(double v) {
