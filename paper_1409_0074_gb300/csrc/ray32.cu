@@ -406,6 +406,7 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
           // two accumulators (elements 0, 2 and 1, 3 of each quad) in one
           // paired FMA per element pair
           float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 2
           for (int k = 0; k < len; k += 4) {
             const float4 l4 = *reinterpret_cast<const float4*>(Li + k);
             const float4 k4 = *reinterpret_cast<const float4*>(kzr + k);
