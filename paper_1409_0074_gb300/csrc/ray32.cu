@@ -110,6 +110,15 @@ __host__ __device__ inline WarpLayout warp_layout(int n, int PP, int RP, int nc)
   return w;
 }
 
+// 2^x by the hardware's base-2 exponential (PTX ex2.approx); the scoring
+// correlations use exp(-d / theta) = 2^(-d log2(e) / theta), with log2(e) / theta
+// formed once per location
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 struct Brent {
   float a, b, x, w, v, fx, fw, fv, d, e;
 };
@@ -215,7 +224,8 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
   const double* xq = P.xref + loc * p;
 
   const double theta = P.theta_loc ? P.theta_loc[loc] : P.theta;
-  const float nit = (float)(-1.0 / theta);
+  // -log2(e) / theta: the correlations' exponentials as one base-2 exponential
+  const float nit2 = (float)(-1.4426950408889634 / theta);
   const double nit64 = -1.0 / theta;
   const float onepg = (float)(1.0 + P.g);
 
@@ -394,7 +404,7 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
             d2 = __ffma2_rn(t01, t01, d2);
             d2 = __ffma2_rn(t23, t23, d2);
           }
-          kzr[k] = __expf((d2.x + d2.y) * nit);
+          kzr[k] = ex2_approx((d2.x + d2.y) * nit2);
         }
       }
       __syncwarp();
@@ -429,7 +439,7 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
 #pragma unroll
         for (int c = 0; c < PP; ++c) { const float t = zc[c] - xf[c]; d = fmaf(t, t, d); }
         const float v = onepg - vs;
-        const float num = ns - __expf(d * nit);
+        const float num = ns - ex2_approx(d * nit2);
         val = v > 0.f ? num * num / v : 0.f;
       }
       __syncwarp();
@@ -520,7 +530,7 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
       const int lim = (sb == 0.f) ? starts[ib] + 1 : nc;
       const int nw = (lim + 31) >> 5;
       const uint32_t bit = 1u << lane;
-#pragma unroll 2
+#pragma unroll 1
       for (int wd = 0; wd < nw; ++wd) {
         const int rr = wd * 32 + lane;
         if (rr < lim && !(mask[wd] & bit)) {
