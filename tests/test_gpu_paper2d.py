@@ -2,8 +2,8 @@
 design of 40,401 points, one ray per step, n = 50, N' = 1000.
 
 FP64 form: identical designs and predictions to the oracle on a sample of the
-99 x 99 predictive grid, for both searches.  FP32-scoring form: the north
-star's bar (RMSE within 1% of the oracle's), missed by the plain form and met
+99 x 99 predictive grid, for both searches.  FP32-scoring form: its accuracy
+bar (RMSE within 1% of the oracle's), missed by the plain form and met
 with precision promotion.  Local inference for theta on the
 GPU's designs (one stage, as in Table 1) against the oracle's predict_mle."""
 import numpy as np

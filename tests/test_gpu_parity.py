@@ -326,8 +326,8 @@ def test_fp64_paper_scale_4d_sample(lagp, paper4d, search):
                    "workload the FP32-form ray RMSE measured 1.3% above the FP64 form's",
                    strict=False)
 def test_fp32_score_ray_paper_scale_4d_sample(lagp, paper4d):
-    """4-d workload (theta = 0.25, cond K_50 up to ~1e7), checked at the north
-    star's 1% bar, which the FP32 form misses at this conditioning."""
+    """4-d workload (theta = 0.25, cond K_50 up to ~1e7), checked at the FP32
+    form's 1% RMSE bar, which it misses at this conditioning."""
     w = _sample(paper4d, 2000)
     g = gpu_run(lagp, w, "ray", "fp32", nrays=4)
     check_fp32_form(w, g, _oracle_4d(w, "ray"), rmse_tol=0.01, max_gap=1e-3)
@@ -427,7 +427,7 @@ def golden_oracle_rmse():
     ("ray", "fp32", 0.01), ("exhaustive", "fp32", 0.01), ("exhaustive", "fp32_tc", 0.01),
     ("ray", "fp64", 1e-12), ("exhaustive", "fp64", 1e-12)])
 def test_rmse_over_the_whole_8d_workload(lagp, large8d, search, precision, tol):
-    """The benchmark spec's accuracy bar on the workload it is quoted on, over all
+    """The FP32 form's accuracy bar on the workload it is quoted on, over all
     100,000 locations (no sampling): the FP32-scoring form's out-of-sample
     RMSE within 1% of the oracle's; the FP64 form, whose designs are the
     oracle's, equal to it up to rounding."""
