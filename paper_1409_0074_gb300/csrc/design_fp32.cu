@@ -180,8 +180,11 @@ __device__ __forceinline__ const float* cand_f(const D32Params& P, const float* 
 
 // Append candidate rank r: FP64 factor row, z, L^{-1}y, FP32 copies, the
 // correlation-cache row K(S_j, c) and entry j of every unselected candidate's w.
+// `best` receives this thread's part of the next search: the ALC of every
+// unselected candidate the thread updates, from the running sums it has just
+// written (the same arithmetic and candidate order as a separate pass).
 __device__ bool add_point32(const D32Params& P, L32& L, const int32_t* cl, const float* crow,
-                            int nc, int r, double* Lg, float* Kc_loc) {
+                            int nc, int r, double* Lg, float* Kc_loc, VI* best) {
   const int tid = threadIdx.x, p = P.p, j = L.j, ld = P.n_max;
   const double* c = P.X + (int64_t)cl[r] * p;
   if (tid < p) L.S64[j * p + tid] = c[tid];
@@ -255,6 +258,8 @@ __device__ bool add_point32(const D32Params& P, L32& L, const int32_t* cl, const
   const float* sj = L.Sf + j * P.PP;
   const float* Lfj = L.Lf;
   const float zj = L.zf[j];
+  VI b;
+  b.v = -1.f; b.v2 = -1.f; b.i = -1;
   for (int q = tid; q < nc; q += blockDim.x) {
     const float kv = __expf(sqdist_row32(cand_f(P, crow, q), sj, P.PP) * L.neg_inv_theta);
     row[q] = kv;
@@ -274,9 +279,16 @@ __device__ bool add_point32(const D32Params& P, L32& L, const int32_t* cl, const
       a1 = fmaf(Lfj[j], kv, a1);
     }
     const float w = a0 + a1;
-    L.vs[q] = fmaf(w, w, L.vs[q]);
-    L.ns[q] = fmaf(w, zj, L.ns[q]);
+    const float nvs = fmaf(w, w, L.vs[q]), nns = fmaf(w, zj, L.ns[q]);
+    L.vs[q] = nvs;
+    L.ns[q] = nns;
+    const float v = L.onepg - nvs;
+    const float num = nns - L.kxc[q];
+    const float alc = v > 0.f ? num * num / v : 0.f;
+    if (alc > b.v) { b.v2 = b.v; b.v = alc; b.i = q; }
+    else if (alc > b.v2) b.v2 = alc;
   }
+  *best = b;
   __syncthreads();
   L.j = j + 1;
   return true;
@@ -284,17 +296,9 @@ __device__ bool add_point32(const D32Params& P, L32& L, const int32_t* cl, const
 
 // ----- exhaustive search, CUDA-core FP32 scoring ---------------------------------
 // ALC_c = (w_c . z - K(c, x))^2 / ((1 + g) - |w_c|^2) from the running sums;
-// the largest score wins, ties to the lower candidate rank.
-__device__ int search_exh32(const L32& L, int nc, double* gap_out) {
-  VI best; best.v = -1.f; best.v2 = -1.f; best.i = -1;
-  for (int r = threadIdx.x; r < nc; r += blockDim.x) {
-    if (L.used[r]) continue;
-    const float v = L.onepg - L.vs[r];
-    const float num = L.ns[r] - L.kxc[r];
-    const float alc = v > 0.f ? num * num / v : 0.f;
-    if (alc > best.v) { best.v2 = best.v; best.v = alc; best.i = r; }
-    else if (alc > best.v2) best.v2 = alc;
-  }
+// the largest score wins, ties to the lower candidate rank.  Each thread's part
+// comes from the update loop of the last appended point (add_point32).
+__device__ int search_exh32(const L32& L, VI best, double* gap_out) {
   VI b = block_best(best, L.red, L.ired);
   *gap_out = (b.v > 0.f && b.v2 >= 0.f) ? (double)((b.v - b.v2) / b.v) : 0.0;
   return b.i;
@@ -376,16 +380,17 @@ __global__ void __launch_bounds__(D32_THREADS, 6) design32(D32Params P) {
     __syncthreads();
 
     bool ok = (n >= P.n0) && (n <= nc) && (n <= ld);
-    for (int r = 0; r < P.n0 && ok; ++r) ok = add_point32(P, L, cl, crow, nc, r, Lg, Kc_loc);
+    VI part;
+    for (int r = 0; r < P.n0 && ok; ++r) ok = add_point32(P, L, cl, crow, nc, r, Lg, Kc_loc, &part);
     for (int j = P.n0; j < n && ok; ++j) {
       double gap = 0.0;
       int ne = 0;
-      int r = search_exh32(L, nc, &gap);
+      int r = search_exh32(L, part, &gap);
       if (tid == 0) {
         if (P.tie_gap) P.tie_gap[loc * ld + (j - P.n0)] = gap;
         if (P.nevals) P.nevals[loc * ld + (j - P.n0)] = ne;
       }
-      ok = (r >= 0) && add_point32(P, L, cl, crow, nc, r, Lg, Kc_loc);
+      ok = (r >= 0) && add_point32(P, L, cl, crow, nc, r, Lg, Kc_loc, &part);
     }
     if (ok) {
       double a = 0.0, b = 0.0, c = 0.0;
