@@ -203,3 +203,30 @@ def test_single_location_uniform_ray(lagp, uneven):
         torch.cuda.synchronize()
         assert torch.equal(one["mean"], big["mean"][m:m + 1])
         assert torch.equal(one["s2"], big["s2"][m:m + 1])
+
+
+@pytest.mark.parametrize("search,precision", FORMS)
+def test_promotion_with_uneven_sizes(lagp, uneven, search, precision):
+    """Precision promotion under uneven n and N' (largest-first work order,
+    and for the tensor-core form the split between two kernels): every
+    location the promoted form changes carries exactly the binary64 form's
+    result, and no more locations change than were promoted."""
+    import torch
+    M = 1000
+    w = uneven
+    args = (to_dev(w.X), to_dev(w.Y), to_dev(w.Xref[:M]), w.n0, int(w.n_arr.max()),
+            int(w.nc_arr.max()), w.theta, w.g)
+    kw = dict(search=search, nrays=8, n_loc=to_dev(w.n_arr[:M], torch.int32),
+              nclose_loc=to_dev(w.nc_arr[:M], torch.int32), want_trace=True)
+    a = lagp.predict(*args, precision=precision + "_promote", want_promoted=True, **kw)
+    b = lagp.predict(*args, precision=precision, **kw)
+    f = lagp.predict(*args, precision="fp64", **kw)
+    torch.cuda.synchronize()
+    na, nb, nf = ({k: v.cpu().numpy() for k, v in o.items() if k != "promoted"}
+                  for o in (a, b, f))
+    changed = ~(np.all(na["selected"] == nb["selected"], axis=1) &
+                (na["mean"].view(np.int64) == nb["mean"].view(np.int64)))
+    assert changed.sum() <= a["promoted"]
+    for m in np.nonzero(changed)[0]:
+        np.testing.assert_array_equal(na["selected"][m], nf["selected"][m])
+        assert na["mean"][m] == nf["mean"][m] and na["s2"][m] == nf["s2"][m]
