@@ -12,6 +12,13 @@
 // Scoring (FP32, through the inverse Cholesky factor, as in design_fp32.cu):
 //   kz_k = exp(-|S_k - z|^2 / theta),  w = L^{-1} kz,
 //   ALC(z) = (w . (L^{-1} k(x)) - K(z, x))^2 / (1 + g - |w|^2).
+// A ray is a straight segment z(s) = a + s d (Sec 4), so every correlation
+// exponent along it is a quadratic in s:
+//   -log2(e) |z(s) - S_k|^2 / theta = c_k + s (b_k + s gam),
+//   c_k = nu |a - S_k|^2,  b_k = 2 nu d . (a - S_k),  gam = nu |d|^2,
+// with nu = -log2(e) / theta.  c_k and b_k are formed once per greedy step;
+// an evaluation then costs two FMAs and one base-2 exponential per design
+// point instead of a p-coordinate distance.
 // L^{-1} (FP32) sits in shared memory as lower-triangular rows padded with
 // zeros to a multiple of 4, so every row is read as float4s.
 // The factor itself grows in FP64 (the partitioned update in factored form,
@@ -85,7 +92,7 @@ __device__ __host__ __forceinline__ int kz_ld(int n) {
 }
 
 struct WarpLayout {
-  int lf, kz, zf, sf, ae, x, sel, gsel, stk, bnd, starts, mask, smask, vm, bytes;
+  int lf, kz, cb, zf, ae, x, sel, gsel, stk, bnd, starts, mask, smask, vm, bytes;
 };
 
 __host__ __device__ inline WarpLayout warp_layout(int n, int PP, int RP, int nc) {
@@ -94,14 +101,18 @@ __host__ __device__ inline WarpLayout warp_layout(int n, int PP, int RP, int nc)
   auto take = [&](int words) { int o = off; off += (words + 3) & ~3; return o; };
   w.lf = take(roff(n));
   w.kz = take(RP * kz_ld(n));
+  // per-ray exponent coefficients c_k then b_k (rows of kz_ld(n)); the k-d
+  // tree walk of the full-scope snap (nodes, then their box distances) runs
+  // after the step's evaluations and reuses this space
+  const int cbw = 2 * RP * kz_ld(n);
+  w.cb = take(cbw > 2 * KD_STACK ? cbw : 2 * KD_STACK);
+  w.stk = w.cb;
+  w.bnd = w.cb + KD_STACK;
   w.zf = take((n + 3) & ~3);
-  w.sf = take(n * PP);
   w.ae = take(2 * RP * PP);
   w.x = take(4 * PP);          // xf, lof, hif, xs
   w.sel = take(n);
   w.gsel = take(n);            // design indices of the selected points
-  w.stk = take(KD_STACK);      // k-d tree walk (full scope): nodes
-  w.bnd = take(KD_STACK);      // and their box distances
   w.starts = take(RP);
   w.mask = take((nc + 31) / 32);
   w.smask = take((nc + 31) / 32);
@@ -199,7 +210,8 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
   float* Lf = base + lay.lf;
   float* kzb = base + lay.kz;
   float* zf = base + lay.zf;
-  float* Sf = base + lay.sf;
+  float* Cb = base + lay.cb;          // c_k of ray r at Cb[r * KP + k]
+  float* Bb = Cb + RP * kz_ld(ldn);   // b_k of ray r at Bb[r * KP + k]
   float* Ab = base + lay.ae;
   float* Eb = Ab + RP * PP;
   float* xf = base + lay.x;
@@ -300,7 +312,6 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
       zy64[j] = (P.Y[gi] - lzy) * inv_d;
       zf[j] = (float)zj;
     }
-    if (lane < PP) Sf[j * PP + lane] = P.Xf[(int64_t)gi * PP + lane];
     __syncwarp();
     ++j;
     return true;
@@ -349,7 +360,7 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
     __syncwarp();
     // ---- segments (FP32): end = A + tau * 10 (A - x), cut at the design's box ----
     const bool ray_live = r < R;
-    float len2 = 0.f;
+    float len2 = 0.f, gam = 0.f, cx = 0.f, bx = 0.f;
     if (ray_live) {
       const float* a = P.Xf + (int64_t)cl[starts[r]] * PP;
       float tau = 1.f;
@@ -359,11 +370,53 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
         else if (dk < 0.f) tau = fminf(tau, (lof[k] - a[k]) / dk);
       }
       tau = fmaxf(tau, 0.f);
+      float av[PP], dv[PP];
+      float cxs = 0.f, bxs = 0.f;
+#pragma unroll
       for (int k = 0; k < PP; ++k) {
         const float ak = a[k];
         const float ek = fmaf(tau, 10.f * (ak - xf[k]), ak);
         if (q == 0) { Ab[r * PP + k] = ak; Eb[r * PP + k] = ek; }
-        len2 = fmaf(ek - ak, ek - ak, len2);
+        av[k] = ak;
+        dv[k] = ek - ak;
+        len2 = fmaf(dv[k], dv[k], len2);
+        const float tx = ak - xf[k];
+        cxs = fmaf(tx, tx, cxs);
+        bxs = fmaf(dv[k], tx, bxs);
+      }
+      // the exponents of K(z(s), x) and of K(z(s), S_k), k < j, as
+      // quadratics in s; quads past j get c = -inf (a zero correlation)
+      gam = nit2 * len2;
+      cx = nit2 * cxs;
+      bx = 2.f * nit2 * bxs;
+      float* cr = Cb + r * KP;
+      float* br = Bb + r * KP;
+      for (int k4 = q; 4 * k4 < j; k4 += G) {
+        float cq[4], bq[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int k = 4 * k4 + u;
+          cq[u] = -__int_as_float(0x7f800000);
+          bq[u] = 0.f;
+          if (k < j) {
+            const float* sk = P.Xf + (int64_t)gsel[k] * PP;
+            float cs = 0.f, bs = 0.f;
+#pragma unroll
+            for (int c = 0; c < PP; c += 4) {
+              const float4 s4 = *reinterpret_cast<const float4*>(sk + c);
+              const float t0 = av[c] - s4.x, t1 = av[c + 1] - s4.y;
+              const float t2 = av[c + 2] - s4.z, t3 = av[c + 3] - s4.w;
+              cs = fmaf(t0, t0, cs); cs = fmaf(t1, t1, cs);
+              cs = fmaf(t2, t2, cs); cs = fmaf(t3, t3, cs);
+              bs = fmaf(dv[c], t0, bs); bs = fmaf(dv[c + 1], t1, bs);
+              bs = fmaf(dv[c + 2], t2, bs); bs = fmaf(dv[c + 3], t3, bs);
+            }
+            cq[u] = nit2 * cs;
+            bq[u] = 2.f * nit2 * bs;
+          }
+        }
+        *reinterpret_cast<float4*>(cr + 4 * k4) = make_float4(cq[0], cq[1], cq[2], cq[3]);
+        *reinterpret_cast<float4*>(br + 4 * k4) = make_float4(bq[0], bq[1], bq[2], bq[3]);
       }
     }
     __syncwarp();
@@ -378,33 +431,21 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
     for (int round = 0; round < RAY_MAX_ROUNDS; ++round) {
       const bool active = phase != PH_DONE;
       if (!__any_sync(0xffffffffu, active)) break;
-      float zc[PP];
-#pragma unroll
-      for (int c = 0; c < PP; ++c) zc[c] = 0.f;
       float* kzr = kzb + r * KP;
       if (active) {
-#pragma unroll
-        for (int c = 0; c < PP; ++c) {
-          const float ac = Ab[r * PP + c];
-          zc[c] = fmaf(s_eval, Eb[r * PP + c] - ac, ac);
-        }
-        // paired FP32 arithmetic (two lanes of work per instruction): the
-        // squared distance is summed as even and odd coordinates, then added
-        float2 nz[PP / 2];
-#pragma unroll
-        for (int c = 0; c < PP; c += 2) nz[c / 2] = make_float2(-zc[c], -zc[c + 1]);
-        for (int k = q; k < j; k += G) {
-          const float* sk = Sf + k * PP;
-          float2 d2 = make_float2(0.f, 0.f);
-#pragma unroll
-          for (int c = 0; c < PP; c += 4) {
-            const float4 s4 = *reinterpret_cast<const float4*>(sk + c);
-            const float2 t01 = __fadd2_rn(make_float2(s4.x, s4.y), nz[c / 2]);
-            const float2 t23 = __fadd2_rn(make_float2(s4.z, s4.w), nz[c / 2 + 1]);
-            d2 = __ffma2_rn(t01, t01, d2);
-            d2 = __ffma2_rn(t23, t23, d2);
-          }
-          kzr[k] = ex2_approx((d2.x + d2.y) * nit2);
+        // kz over quads of design points, two exponents per paired FMA
+        const float* cr = Cb + r * KP;
+        const float* br = Bb + r * KP;
+        const float2 s2v = make_float2(s_eval, s_eval), g2 = make_float2(gam, gam);
+        for (int k4 = q; 4 * k4 < j; k4 += G) {
+          const float4 c4 = *reinterpret_cast<const float4*>(cr + 4 * k4);
+          const float4 b4 = *reinterpret_cast<const float4*>(br + 4 * k4);
+          const float2 t01 = __ffma2_rn(s2v, g2, make_float2(b4.x, b4.y));
+          const float2 t23 = __ffma2_rn(s2v, g2, make_float2(b4.z, b4.w));
+          const float2 e01 = __ffma2_rn(s2v, t01, make_float2(c4.x, c4.y));
+          const float2 e23 = __ffma2_rn(s2v, t23, make_float2(c4.z, c4.w));
+          *reinterpret_cast<float4*>(kzr + 4 * k4) =
+              make_float4(ex2_approx(e01.x), ex2_approx(e01.y), ex2_approx(e23.x), ex2_approx(e23.y));
         }
       }
       __syncwarp();
@@ -435,11 +476,8 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
       }
       float val = 0.f;
       if (active) {
-        float d = 0.f;
-#pragma unroll
-        for (int c = 0; c < PP; ++c) { const float t = zc[c] - xf[c]; d = fmaf(t, t, d); }
         const float v = onepg - vs;
-        const float num = ns - ex2_approx(d * nit2);
+        const float num = ns - ex2_approx(fmaf(s_eval, fmaf(s_eval, gam, bx), cx));
         val = v > 0.f ? num * num / v : 0.f;
       }
       __syncwarp();
