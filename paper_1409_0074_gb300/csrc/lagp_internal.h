@@ -225,6 +225,8 @@ cudaError_t launch_ray32(const DesignArgs& a, cudaStream_t s);
 int exh_tc_max_n();
 cudaError_t launch_exh_tc(const DesignArgs& a, cudaStream_t s);
 size_t ray32_g64_doubles(int n_max);
+// warps per CTA of the ray kernel when no launch choice is stored for a shape
+int ray32_default_warps(int p, int n_max, int nc_max, int nrays);
 // FP32-scoring exhaustive search with incremental CUDA-core scoring
 // (design_fp32.cu), n_max <= 128: every location of the LAGP_FP32_SCORE form,
 // the n > exh_tc_max_n() locations of LAGP_FP32_SCORE_TC.

@@ -92,7 +92,7 @@ __device__ __host__ __forceinline__ int kz_ld(int n) {
 }
 
 struct WarpLayout {
-  int lf, kz, cb, zf, ae, x, sel, gsel, stk, bnd, starts, mask, smask, vm, bytes;
+  int lf, kz, cb, zf, tau, x, gsel, stk, bnd, starts, mask, smask, vm, bytes;
 };
 
 __host__ __device__ inline WarpLayout warp_layout(int n, int PP, int RP, int nc) {
@@ -109,9 +109,8 @@ __host__ __device__ inline WarpLayout warp_layout(int n, int PP, int RP, int nc)
   w.stk = w.cb;
   w.bnd = w.cb + KD_STACK;
   w.zf = take((n + 3) & ~3);
-  w.ae = take(2 * RP * PP);
+  w.tau = take(RP);            // each ray's segment: end = a + tau * 10 (a - x)
   w.x = take(4 * PP);          // xf, lof, hif, xs
-  w.sel = take(n);
   w.gsel = take(n);            // design indices of the selected points
   w.starts = take(RP);
   w.mask = take((nc + 31) / 32);
@@ -212,13 +211,11 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
   float* zf = base + lay.zf;
   float* Cb = base + lay.cb;          // c_k of ray r at Cb[r * KP + k]
   float* Bb = Cb + RP * kz_ld(ldn);   // b_k of ray r at Bb[r * KP + k]
-  float* Ab = base + lay.ae;
-  float* Eb = Ab + RP * PP;
+  float* taub = base + lay.tau;
   float* xf = base + lay.x;
   float* lof = xf + PP;
   float* hif = lof + PP;
   float* xs = hif + PP;
-  int* sel = reinterpret_cast<int*>(base + lay.sel);      // candidate ranks (-1: not one)
   int* gsel = reinterpret_cast<int*>(base + lay.gsel);    // design indices
   int* stk = reinterpret_cast<int*>(base + lay.stk);
   float* bnd = base + lay.bnd;
@@ -304,7 +301,6 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
     if (lane == 0) {
       Lj[j] = inv_d;
       Lfj[j] = (float)inv_d;
-      sel[j] = rr;
       gsel[j] = gi;
       if (rr >= 0) mask[rr >> 5] |= 1u << (rr & 31);
       const double zj = (kx64[j] - lz) * inv_d;
@@ -370,13 +366,13 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
         else if (dk < 0.f) tau = fminf(tau, (lof[k] - a[k]) / dk);
       }
       tau = fmaxf(tau, 0.f);
+      if (q == 0) taub[r] = tau;
       float av[PP], dv[PP];
       float cxs = 0.f, bxs = 0.f;
 #pragma unroll
       for (int k = 0; k < PP; ++k) {
         const float ak = a[k];
         const float ek = fmaf(tau, 10.f * (ak - xf[k]), ak);
-        if (q == 0) { Ab[r * PP + k] = ak; Eb[r * PP + k] = ek; }
         av[k] = ak;
         dv[k] = ek - ak;
         len2 = fmaf(dv[k], dv[k], len2);
@@ -516,7 +512,12 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
       else if (a_r > second) second = a_r;
     }
     const float sb = __shfl_sync(0xffffffffu, s_star, ib * G);
-    if (lane < PP) xs[lane] = fmaf(sb, Eb[ib * PP + lane] - Ab[ib * PP + lane], Ab[ib * PP + lane]);
+    if (lane < PP) {
+      // the best ray's segment again, in the same operations as above
+      const float ak = P.Xf[(int64_t)cl[starts[ib]] * PP + lane];
+      const float ek = fmaf(taub[ib], 10.f * (ak - xf[lane]), ak);
+      xs[lane] = fmaf(sb, ek - ak, ak);
+    }
     __syncwarp();
     // ---- snap: nearest allowed unselected candidate (ties to the lower rank) ----
     // allowed: not one of this step's ray starts unless it coincides with x*;
@@ -662,6 +663,31 @@ __global__ void __launch_bounds__(RW * 32, 20 / RW) ray32_kernel(RayParams P) {
     ray32_location<RP, PP>(P, P.order ? (int64_t)P.order[it] : (int64_t)it, base, Lg);
     __syncwarp();
   }
+}
+
+// Warps per CTA that let the most locations reside on an SM at this shape:
+// shared memory decides, under the launch bound's 20 warps per SM; ties go to
+// 2, then 4, then 1, and 2 is the answer when no device can be queried.
+int ray32_default_warps(int p, int n_max, int nc_max, int nrays) {
+  int dev = 0, smem_sm = 0, reserved = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+          cudaSuccess ||
+      cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return 2;
+  }
+  int RP = 2;
+  while (RP < nrays) RP <<= 1;
+  const size_t wb = (size_t)warp_layout(n_max, (p + 3) / 4 * 4, RP, nc_max).bytes;
+  int best = 2, best_warps = -1;
+  for (const int rw : {2, 4, 1}) {
+    int ctas = (int)((size_t)smem_sm / (rw * wb + (size_t)reserved));
+    if (ctas > 20 / rw) ctas = 20 / rw;
+    if (ctas * rw > best_warps) { best_warps = ctas * rw; best = rw; }
+  }
+  return best;
 }
 
 size_t ray32_g64_doubles(int n_max) { return (size_t)tri(n_max) + 5 * (size_t)n_max; }

@@ -130,7 +130,9 @@ Tune lookup_tune(int p, int n_max, int nc_max, int nrays, int search, int uneven
         e.search == search && e.uneven == uneven)
       return e.t;
   }
-  return default_tune();
+  Tune t = default_tune();
+  if (search != LAGP_EXHAUSTIVE) t.ray_warps = ray32_default_warps(p, n_max, nc_max, nrays);
+  return t;
 }
 
 void store_tune(int p, int n_max, int nc_max, int nrays, int search, int uneven, const Tune& t) {
