@@ -34,7 +34,10 @@
 // A batch with fewer location tiles than SMs splits the design into segments,
 // one CTA each (grid y); the segments of a location append to its buffer
 // through a global counter (passes are rare), and knn_tc_join decides its
-// validity once all of them are done.  The buffered set is the same.
+// validity once all of them are done.  The buffered set is the same.  A larger
+// batch runs whole waves of one CTA per SM unsplit and splits only the tiles
+// of its last, partial wave, so that they spread over the SMs that would
+// otherwise idle.
 //
 // err bounds |d_tc - d64| for the 3xTF32 contraction: operand splitting
 // (3 * 2^-22 |A_k B_k| per term), FP32 accumulation over 3K products
@@ -181,7 +184,7 @@ knn_tc(const float* __restrict__ Btiles, int64_t ntiles, int p, const double* __
        int64_t M, const double* __restrict__ center, const unsigned* __restrict__ maxn2_bits,
        int nc_max, const int32_t* __restrict__ nc_loc, int cap, const float* __restrict__ pilot,
        KnnEntry* __restrict__ buf, int32_t* __restrict__ cnt_out, int32_t* __restrict__ seg_out,
-       unsigned* __restrict__ status) {
+       unsigned* __restrict__ status, int64_t tile0) {
   using L = KtSmem<KA>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
@@ -200,7 +203,7 @@ knn_tc(const float* __restrict__ Btiles, int64_t ntiles, int p, const double* __
   int* abort_flag = reinterpret_cast<int*>(smem + L::MISC_OFF + 4);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t q0 = (int64_t)blockIdx.x * KT_M;
+  const int64_t q0 = (tile0 + (int64_t)blockIdx.x) * KT_M;
   // design segment of this CTA: tiles [t_lo, t_lo + nt) (the whole design
   // unless the launch splits it over gridDim.y CTAs per location tile)
   const int64_t t_lo = SPLIT ? (int64_t)blockIdx.y * ntiles / gridDim.y : 0;
@@ -416,10 +419,11 @@ knn_tc(const float* __restrict__ Btiles, int64_t ntiles, int p, const double* __
 // After a split launch: a location is valid when its buffer did not overflow
 // and at least N' of its entries lie at or below the pilot value; its entries
 // are then the first count of the buffer (one quarter, as finalize reads it).
-__global__ void knn_tc_join(int64_t M, int nc_max, const int32_t* __restrict__ nc_loc, int cap,
+__global__ void knn_tc_join(int64_t q_begin, int64_t M, int nc_max,
+                            const int32_t* __restrict__ nc_loc, int cap,
                             const float* __restrict__ pilot, int32_t* __restrict__ cnt,
                             int32_t* __restrict__ seg, const unsigned* __restrict__ status) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t q = q_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= M) return;
   const int total = seg[q * KT_GROUPS], below = seg[q * KT_GROUPS + 1];
   const int nc = nc_loc ? nc_loc[q] : nc_max;
@@ -491,36 +495,51 @@ cudaError_t launch_knn_tc(int64_t Npad, int p, const double* xref, int64_t M, in
                           const int32_t* nc_loc, int cap, const Workspace& ws, cudaStream_t s) {
   const int KA = kt_ka(p);
   const int64_t ntiles = Npad / KT_N;
-  const unsigned grid = (unsigned)((M + KT_M - 1) / KT_M);
+  const int64_t tiles = (M + KT_M - 1) / KT_M;
   KnnEntry* kbuf = reinterpret_cast<KnnEntry*>(ws.knn_buf);
   cudaError_t err;
-  // A small batch has fewer location tiles than SMs: split the design into
-  // segments so that about two CTAs per SM run, each segment at least 64 tiles.
   int sms = 0, dev = 0;
   if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
   if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
     return err;
-  int64_t nseg = (2 * (int64_t)sms + grid - 1) / grid;
+  // One CTA (all 512 TMEM columns) per SM.  Tiles [0, body) run unsplit in
+  // whole waves; the remaining tiles split the design into nseg segments of at
+  // least 64 design tiles each.  A small batch (fewer tiles than SMs) splits
+  // every tile, about two CTAs per SM; a larger one splits the tiles of its
+  // last, partial wave over the SMs that wave leaves idle.
+  int64_t body = tiles, nseg = 1;
+  if (tiles < sms) {
+    nseg = (2 * (int64_t)sms + tiles - 1) / tiles;
+    body = 0;
+  } else if (tiles % sms != 0) {
+    nseg = sms / (tiles % sms);
+    body = tiles - tiles % sms;
+  }
   if (nseg > ntiles / 64) nseg = ntiles / 64;
   if (nseg > 65535) nseg = 65535;
-  if (nseg < 1) nseg = 1;
-  const int split = nseg > 1 ? 1 : 0;
-  if (split && (err = cudaMemsetAsync(ws.knn_seg, 0, sizeof(int32_t) * KT_GROUPS * M, s)) !=
-                   cudaSuccess)
+  if (nseg < 2) { nseg = 1; body = tiles; }
+  const int64_t rest = tiles - body, q_split = body * KT_M;
+  if (rest > 0 && (err = cudaMemsetAsync(ws.knn_seg + KT_GROUPS * q_split, 0,
+                                         sizeof(int32_t) * KT_GROUPS * (M - q_split), s)) !=
+                      cudaSuccess)
     return err;
-  const dim3 g3(grid, (unsigned)nseg);
   switch (KA) {
 #define KT_CASE(V)                                                                              \
   case V: {                                                                                     \
     const size_t sm = KtSmem<V>::BYTES;                                                         \
-    auto kern = split ? knn_tc<V, true> : knn_tc<V, false>;                                     \
-    err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);     \
-    if (err != cudaSuccess) return err;                                                         \
-    prof_begin("knn_tc", s);                                                                    \
-    kern<<<g3, KT_THREADS, sm, s>>>(ws.Btc, ntiles, p, xref, M, ws.center, ws.maxn2, nc_max,    \
-                                    nc_loc, cap, ws.knn_thr, kbuf, ws.knn_cnt, ws.knn_seg,      \
-                                    ws.status);                                                 \
-    prof_end(s);                                                                                \
+    for (int part = 0; part < 2; ++part) {                                                      \
+      const int64_t n_part = part == 0 ? body : rest;                                           \
+      if (n_part == 0) continue;                                                                \
+      auto kern = part == 0 ? knn_tc<V, false> : knn_tc<V, true>;                               \
+      err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);   \
+      if (err != cudaSuccess) return err;                                                       \
+      const dim3 g3((unsigned)n_part, part == 0 ? 1u : (unsigned)nseg);                         \
+      prof_begin("knn_tc", s);                                                                  \
+      kern<<<g3, KT_THREADS, sm, s>>>(ws.Btc, ntiles, p, xref, M, ws.center, ws.maxn2, nc_max,  \
+                                      nc_loc, cap, ws.knn_thr, kbuf, ws.knn_cnt, ws.knn_seg,    \
+                                      ws.status, part == 0 ? 0 : body);                         \
+      prof_end(s);                                                                              \
+    }                                                                                           \
     break;                                                                                      \
   }
     KT_CASE(8)
@@ -530,10 +549,10 @@ cudaError_t launch_knn_tc(int64_t Npad, int p, const double* xref, int64_t M, in
     default:
       return cudaErrorInvalidValue;
   }
-  if (split) {
+  if (rest > 0) {
     prof_begin("knn_tc_join", s);
-    knn_tc_join<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(M, nc_max, nc_loc, cap, ws.knn_thr,
-                                                              ws.knn_cnt, ws.knn_seg, ws.status);
+    knn_tc_join<<<(unsigned)((M - q_split + 255) / 256), 256, 0, s>>>(
+        q_split, M, nc_max, nc_loc, cap, ws.knn_thr, ws.knn_cnt, ws.knn_seg, ws.status);
     prof_end(s);
   }
   prof_begin("knn_finalize", s);
