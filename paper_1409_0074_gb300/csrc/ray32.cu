@@ -64,7 +64,7 @@ struct RayParams {
   int32_t* selected;
   double* tie_gap;
   int32_t* nevals;
-  double* g64;          // per warp slot: packed L^{-1} (n(n+1)/2) then kx, z, zy, kvec, l (n each)
+  double* g64;          // per warp slot: packed L^{-1} (n(n+1)/2) then z, L^{-1} y (n each)
   int64_t g64_stride;
   unsigned* status;
   unsigned* queue;      // work counter (zero at launch)
@@ -102,8 +102,9 @@ __host__ __device__ inline WarpLayout warp_layout(int n, int PP, int RP, int nc)
   w.lf = take(roff(n));
   w.kz = take(RP * kz_ld(n));
   // per-ray exponent coefficients c_k then b_k (rows of kz_ld(n)); the k-d
-  // tree walk of the full-scope snap (nodes, then their box distances) runs
-  // after the step's evaluations and reuses this space
+  // tree walk of the full-scope snap (nodes, then their box distances) and
+  // the factor update's two binary64 work vectors (n each) run after the
+  // step's evaluations and reuse this space
   const int cbw = 2 * RP * kz_ld(n);
   w.cb = take(cbw > 2 * KD_STACK ? cbw : 2 * KD_STACK);
   w.stk = w.cb;
@@ -225,11 +226,8 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
   double* vmin = reinterpret_cast<double*>(base + lay.vm);
   const int KP = kz_ld(ldn);
 
-  double* kx64 = Lg + tri(ldn);
-  double* z64 = kx64 + ldn;
+  double* z64 = Lg + tri(ldn);
   double* zy64 = z64 + ldn;
-  double* kv64 = zy64 + ldn;
-  double* l64 = kv64 + ldn;
   const double* xq = P.xref + loc * p;
 
   const double theta = P.theta_loc ? P.theta_loc[loc] : P.theta;
@@ -256,12 +254,18 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
   if (lane == 0) *vmin = INFINITY;
 
   // ---- append design point gi (candidate rank rr, or -1) (FP64 factor row) ----
+  // k_j(x_new) and l = L_j^{-1} k_j(x_new) live in shared memory, in the
+  // coefficient region, which no evaluation uses while a point is appended
+  double* kvs = reinterpret_cast<double*>(Cb);
+  double* ls = kvs + ldn;
   auto add_point = [&](int gi, int rr) -> bool {
     const double* c64 = P.X + (int64_t)gi * p;
+    double kxj = 0.0;   // K(x_new, x), on lane j mod 32
     for (int i = lane; i <= j; i += 32) {
-      if (i < j) kv64[i] = corr64_fast(P.X + (int64_t)gsel[i] * p, c64, p, nit64);
-      else kx64[j] = corr64_fast(c64, xq, p, nit64);
+      if (i < j) kvs[i] = corr64_fast(P.X + (int64_t)gsel[i] * p, c64, p, nit64);
+      else kxj = corr64_fast(c64, xq, p, nit64);
     }
+    kxj = __shfl_sync(0xffffffffu, kxj, j & 31);
     __syncwarp();
     // l = L_j^{-1} k_j(x_new); v = 1 + g - |l|^2, d = sqrt(v), and by forward
     // substitution z_j = (K(x_new, x) - l . z) / d, (L^{-1} y)_j =
@@ -270,8 +274,8 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
     // evaluates the scalar tail.
     double vv = 0.0, lz = 0.0, lzy = 0.0;
     for (int i = lane; i < j; i += 32) {
-      const double acc = dot64_ilp(Lg + tri(i), kv64, i + 1);
-      l64[i] = acc;
+      const double acc = dot64_ilp(Lg + tri(i), kvs, i + 1);
+      ls[i] = acc;
       vv = fma(acc, acc, vv);
       lz = fma(acc, z64[i], lz);
       lzy = fma(acc, zy64[i], lzy);
@@ -290,10 +294,10 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
       double a0 = 0.0, a1 = 0.0;
       int i = k;
       for (; i + 1 < j; i += 2) {
-        a0 = fma(l64[i], Lg[tri(i) + k], a0);
-        a1 = fma(l64[i + 1], Lg[tri(i + 1) + k], a1);
+        a0 = fma(ls[i], Lg[tri(i) + k], a0);
+        a1 = fma(ls[i + 1], Lg[tri(i + 1) + k], a1);
       }
-      if (i < j) a0 = fma(l64[i], Lg[tri(i) + k], a0);
+      if (i < j) a0 = fma(ls[i], Lg[tri(i) + k], a0);
       const double rk = -(a0 + a1) * inv_d;
       Lj[k] = rk;
       Lfj[k] = (float)rk;
@@ -303,7 +307,7 @@ __device__ __forceinline__ void ray32_location(const RayParams& P, const int64_t
       Lfj[j] = (float)inv_d;
       gsel[j] = gi;
       if (rr >= 0) mask[rr >> 5] |= 1u << (rr & 31);
-      const double zj = (kx64[j] - lz) * inv_d;
+      const double zj = (kxj - lz) * inv_d;
       z64[j] = zj;
       zy64[j] = (P.Y[gi] - lzy) * inv_d;
       zf[j] = (float)zj;
@@ -690,7 +694,7 @@ int ray32_default_warps(int p, int n_max, int nc_max, int nrays) {
   return best;
 }
 
-size_t ray32_g64_doubles(int n_max) { return (size_t)tri(n_max) + 5 * (size_t)n_max; }
+size_t ray32_g64_doubles(int n_max) { return (size_t)tri(n_max) + 2 * (size_t)n_max; }
 
 // Warp slots for a chunk: at least one CTA of the widest choice (4 warps) and a
 // multiple of 4, so that every warp of every launched CTA owns a slot.
