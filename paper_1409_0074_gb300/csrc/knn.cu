@@ -412,8 +412,77 @@ knn_stream(const float* __restrict__ Xf, const float* __restrict__ nx, int64_t N
 // Exact ranking: binary64 distances in the oracle's order, bitonic sort of
 // (d64, index), first N' indices out.  Distances are non-negative, so their
 // IEEE bit patterns order like the values: the sort compares 64-bit integers
-// (FP64 compares would run on GB300's narrow FP64 pipe).
+// (FP64 compares would run on GB300's narrow FP64 pipe).  Up to 1024 pairs
+// are sorted in registers, four per thread (element 4 t + u on thread t):
+// strides 1 and 2 inside a thread, 4 to 64 between the lanes of a warp by
+// shuffles, 128 to 512 through shared memory.  Larger sets take the same
+// network entirely in shared memory.  The real pairs are distinct (distinct
+// indices), so either way the order is the unique sorted one.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ bool kv_less(unsigned long long ka, int32_t ia, unsigned long long kb,
+                                        int32_t ib) {
+  return ka < kb || (ka == kb && ia < ib);
+}
+
+// Sorts the 1024 pairs in kr/ir (four per thread) and leaves them in order in
+// key/idx[0..1024), which must hold 1024 entries; blockDim.x == 256.
+__device__ __forceinline__ void rank_sort1024(unsigned long long* kr, int32_t* ir,
+                                              unsigned long long* key, int32_t* idx) {
+  const int t = threadIdx.x;
+  for (int k = 2; k <= 1024; k <<= 1) {
+    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+      if (jj >= 4) {
+        const int pt = t ^ (jj >> 2);   // the partner thread, same u
+        unsigned long long pk[4];
+        int32_t pi[4];
+        if (jj >= 128) {                 // another warp: through shared memory
+          __syncthreads();
+#pragma unroll
+          for (int u = 0; u < 4; ++u) { key[4 * t + u] = kr[u]; idx[4 * t + u] = ir[u]; }
+          __syncthreads();
+#pragma unroll
+          for (int u = 0; u < 4; ++u) { pk[u] = key[4 * pt + u]; pi[u] = idx[4 * pt + u]; }
+        } else {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            pk[u] = __shfl_xor_sync(0xffffffffu, kr[u], jj >> 2);
+            pi[u] = __shfl_xor_sync(0xffffffffu, ir[u], jj >> 2);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = 4 * t + u;
+          // the lower element of an ascending pair (or the upper of a
+          // descending one) keeps the smaller
+          const bool keep_min = ((i & jj) == 0) == ((i & k) == 0);
+          const bool p_less = kv_less(pk[u], pi[u], kr[u], ir[u]);
+          if (keep_min ? p_less : !p_less) { kr[u] = pk[u]; ir[u] = pi[u]; }
+        }
+      } else {
+        // pairs (u, u + jj) inside the thread, with constant register indices
+        auto ce = [&](unsigned long long& ka, int32_t& ia, unsigned long long& kb, int32_t& ib,
+                      int u) {
+          const bool up = ((4 * t + u) & k) == 0;
+          if (kv_less(kb, ib, ka, ia) == up) {
+            const unsigned long long tk = ka; ka = kb; kb = tk;
+            const int32_t ti = ia; ia = ib; ib = ti;
+          }
+        };
+        if (jj == 2) {
+          ce(kr[0], ir[0], kr[2], ir[2], 0);
+          ce(kr[1], ir[1], kr[3], ir[3], 1);
+        } else {
+          ce(kr[0], ir[0], kr[1], ir[1], 0);
+          ce(kr[2], ir[2], kr[3], ir[3], 2);
+        }
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < 4; ++u) { key[4 * t + u] = kr[u]; idx[4 * t + u] = ir[u]; }
+  __syncthreads();
+}
 __global__ void __launch_bounds__(256)
 knn_rank(const double* __restrict__ X, int p, const double* __restrict__ xref, int64_t M,
          int nc_max, const int32_t* __restrict__ nc_loc, int cap,
@@ -432,6 +501,24 @@ knn_rank(const double* __restrict__ X, int p, const double* __restrict__ xref, i
   while (sz < c) sz <<= 1;
   __syncthreads();
   const KnnEntry* e = buf + q * (int64_t)cap;
+  // the register form needs 1024 slots of shared memory for its exchanges
+  if (sz <= 1024 && cap >= 1024 && blockDim.x == 256) {
+    unsigned long long kr[4];
+    int32_t ir[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = 4 * threadIdx.x + u;
+      if (i < c) {
+        const int32_t gi = e[i].idx;
+        kr[u] = (unsigned long long)__double_as_longlong(sqdist64(X + (int64_t)gi * p, xq, p));
+        ir[u] = gi;
+      } else {
+        kr[u] = ~0ull;
+        ir[u] = 0x7fffffff;
+      }
+    }
+    rank_sort1024(kr, ir, key, idx);
+  } else {
   for (int i = threadIdx.x; i < sz; i += blockDim.x) {
     if (i < c) {
       int32_t gi = e[i].idx;
@@ -460,6 +547,7 @@ knn_rank(const double* __restrict__ X, int p, const double* __restrict__ xref, i
       }
       __syncthreads();
     }
+  }
   }
   if (c < nc && threadIdx.x == 0) atomicOr(status, LAGP_DEV_KNN_OVERFLOW);
   // ranks this location lacks (a flagged overflow or timeout) repeat a valid
