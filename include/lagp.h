@@ -359,7 +359,9 @@ int laGP_build_and_predict_host(const double* design, const double* y, int64_t N
  * (n_loc / nclose_loc given), and the fraction of resident CTAs per SM the
  * exhaustive kernels keep (1 or 1/2).  A process-wide table keyed by
  * (p, n, N_close, nrays, search, uneven) holds the choice; without an entry
- * the defaults are 2 warps, largest-first, all resident CTAs.
+ * the defaults are largest-first and all resident CTAs, with the ray kernel's
+ * warps per CTA the choice that lets the most of its warps reside on an SM
+ * at that shape (ties to 2, then 4, then 1; 2 when no device can be queried).
  *
  * laGP_autotune times every choice that applies to these arguments on the
  * first min(M, chunk) locations (one kNN pass, then for each choice one
