@@ -49,6 +49,7 @@
 #include "common.cuh"
 #include "knn_common.cuh"
 #include "lagp_internal.h"
+#include "launch_plan.h"
 
 namespace lagp {
 
@@ -502,22 +503,9 @@ cudaError_t launch_knn_tc(int64_t Npad, int p, const double* xref, int64_t M, in
   if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
   if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
     return err;
-  // One CTA (all 512 TMEM columns) per SM.  Tiles [0, body) run unsplit in
-  // whole waves; the remaining tiles split the design into nseg segments of at
-  // least 64 design tiles each.  A small batch (fewer tiles than SMs) splits
-  // every tile, about two CTAs per SM; a larger one splits the tiles of its
-  // last, partial wave over the SMs that wave leaves idle.
+  // whole waves unsplit, the rest split over the SMs (launch_plan.h)
   int64_t body = tiles, nseg = 1;
-  if (tiles < sms) {
-    nseg = (2 * (int64_t)sms + tiles - 1) / tiles;
-    body = 0;
-  } else if (tiles % sms != 0) {
-    nseg = sms / (tiles % sms);
-    body = tiles - tiles % sms;
-  }
-  if (nseg > ntiles / 64) nseg = ntiles / 64;
-  if (nseg > 65535) nseg = 65535;
-  if (nseg < 2) { nseg = 1; body = tiles; }
+  knn_tc_plan(tiles, sms, ntiles, &body, &nseg);
   const int64_t rest = tiles - body, q_split = body * KT_M;
   if (rest > 0 && (err = cudaMemsetAsync(ws.knn_seg + KT_GROUPS * q_split, 0,
                                          sizeof(int32_t) * KT_GROUPS * (M - q_split), s)) !=

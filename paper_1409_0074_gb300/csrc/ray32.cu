@@ -36,6 +36,7 @@
 #include "common.cuh"
 #include "kdtree.cuh"
 #include "lagp_internal.h"
+#include "launch_plan.h"
 
 namespace lagp {
 
@@ -685,13 +686,7 @@ int ray32_default_warps(int p, int n_max, int nc_max, int nrays) {
   int RP = 2;
   while (RP < nrays) RP <<= 1;
   const size_t wb = (size_t)warp_layout(n_max, (p + 3) / 4 * 4, RP, nc_max).bytes;
-  int best = 2, best_warps = -1;
-  for (const int rw : {2, 4, 1}) {
-    int ctas = (int)((size_t)smem_sm / (rw * wb + (size_t)reserved));
-    if (ctas > 20 / rw) ctas = 20 / rw;
-    if (ctas * rw > best_warps) { best_warps = ctas * rw; best = rw; }
-  }
-  return best;
+  return warps_per_cta_for_residency(wb, (size_t)smem_sm, (size_t)reserved, 20);
 }
 
 size_t ray32_g64_doubles(int n_max) { return (size_t)tri(n_max) + 2 * (size_t)n_max; }
