@@ -12,10 +12,12 @@ Local inference for the lengthscale (Sec 5, Eq. gpk): loglik, mle_theta and
 predict_mle, pinned in tests/test_oracle_mle.py.
 
 Every function here is pinned by tests under tests/ against closed forms,
-brute force or library routines (numpy, scipy).  Ray-search designs are pinned
-only piecewise (round-robin offsets, segments, Brent minima, snapping): the
-paper prints no worked ray example, so whole ray designs are "parity unpinned"
-beyond those pieces.
+brute force or library routines (numpy, scipy).  The paper prints no worked ray
+example, so ray-search designs are pinned piece by piece (round-robin offsets,
+segments, Brent minima, snapping) and as whole designs against a replay of
+every step from independent parts: a numpy kNN sort, the hand-worked offsets,
+ALC as a directly re-solved variance drop, scipy's bounded Brent minimiser and
+a brute-force snap (tests/test_oracle_ray_designs.py).
 """
 import contextlib
 import ctypes as C
