@@ -224,7 +224,7 @@ def source_hash(texts):
 def ray32_traffic():
     """DRAM bytes of one full-size ray32 launch (100,000 locations)."""
     return profile_traffic("ray32_sinusoid8d_N1e6_M1e5_dram.md",
-                           ("ray32.cu", "common.cuh", "kdtree.cuh"),
+                           ("ray32.cu", "ray32_layout.h", "common.cuh", "kdtree.cuh"),
                            "traffic_bytes_per_launch")
 
 

@@ -37,6 +37,7 @@
 #include "kdtree.cuh"
 #include "lagp_internal.h"
 #include "launch_plan.h"
+#include "ray32_layout.h"
 
 namespace lagp {
 
@@ -76,51 +77,6 @@ struct RayParams {
   int32_t* promote;     // binary64 re-solve list, or null (promotion off)
   unsigned* promote_count;
 };
-
-// start of row i in the zero-padded FP32 row storage (rows of length
-// (i+1) rounded up to a multiple of 4)
-__device__ __host__ __forceinline__ int roff(int i) {
-  const int a = i >> 2, b = i & 3;
-  return 4 * (i + 2 * a * (a - 1) + a * b);
-}
-__device__ __host__ __forceinline__ int tri(int i) { return i * (i + 1) / 2; }
-// row length of the kz buffer: a multiple of 4 whose quarter is odd, so that
-// the rays' float4 reads fall on different banks
-__device__ __host__ __forceinline__ int kz_ld(int n) {
-  int k = (n + 3) & ~3;
-  if (((k >> 2) & 1) == 0) k += 4;
-  return k;
-}
-
-struct WarpLayout {
-  int lf, kz, cb, zf, tau, x, gsel, stk, bnd, starts, mask, smask, vm, bytes;
-};
-
-__host__ __device__ inline WarpLayout warp_layout(int n, int PP, int RP, int nc) {
-  WarpLayout w;
-  int off = 0;   // in 4-byte words, float region first (16-byte aligned pieces)
-  auto take = [&](int words) { int o = off; off += (words + 3) & ~3; return o; };
-  w.lf = take(roff(n));
-  w.kz = take(RP * kz_ld(n));
-  // per-ray exponent coefficients c_k then b_k (rows of kz_ld(n)); the k-d
-  // tree walk of the full-scope snap (nodes, then their box distances) and
-  // the factor update's two binary64 work vectors (n each) run after the
-  // step's evaluations and reuse this space
-  const int cbw = 2 * RP * kz_ld(n);
-  w.cb = take(cbw > 2 * KD_STACK ? cbw : 2 * KD_STACK);
-  w.stk = w.cb;
-  w.bnd = w.cb + KD_STACK;
-  w.zf = take((n + 3) & ~3);
-  w.tau = take(RP);            // each ray's segment: end = a + tau * 10 (a - x)
-  w.x = take(4 * PP);          // xf, lof, hif, xs
-  w.gsel = take(n);            // design indices of the selected points
-  w.starts = take(RP);
-  w.mask = take((nc + 31) / 32);
-  w.smask = take((nc + 31) / 32);
-  w.vm = take(2);              // smallest binary64 pivot of the location (lane 0)
-  w.bytes = off * 4;
-  return w;
-}
 
 // 2^x by the hardware's base-2 exponential (PTX ex2.approx); the scoring
 // correlations use exp(-d / theta) = 2^(-d log2(e) / theta), with log2(e) / theta
